@@ -1,0 +1,112 @@
+"""Pins of the oracle's POD (Sec. 4.1) and block-incremental SVD (Sec. 4.2)."""
+import numpy as np
+import pytest
+
+from oracle import fom, pod
+from workloads import make_problem, problem_for
+
+
+@pytest.fixture(scope="module")
+def c1_blocks():
+    p = problem_for("c1")
+    blocks = [fom.fom_march(fom.affine_operator(p.rowptr, p.col, p.vals, p.theta(mu)),
+                            p.dt, p.B, p.F, p.u0) for mu in p.train_mu]
+    return p, blocks
+
+
+def test_exact_pod_identities(c1_blocks):
+    p, blocks = c1_blocks
+    U = pod.snapshot_matrix(blocks)
+    r = pod.pod_exact(blocks, p.ns, p.nt)
+    W, s, V = r["W"], r["sigma"], r["V"]
+    assert np.abs(W.T @ W - np.eye(W.shape[1])).max() < 1e-13
+    assert np.abs(V.T @ V - np.eye(V.shape[1])).max() < 1e-13
+    # Eq. SVDsummation and sum sigma^2 = ||U||_F^2
+    assert np.abs(W @ np.diag(s) @ V.T - U).max() < 1e-12 * s[0]
+    assert abs((s ** 2).sum() - np.linalg.norm(U) ** 2) < 1e-12 * (s ** 2).sum()
+    # Eckart-Young optimality of Eq. POD: the residual energy is the tail
+    for ns in (1, 4, 8, 20):
+        Ph = W[:, :ns]
+        res = np.linalg.norm(U - Ph @ (Ph.T @ U)) ** 2
+        assert abs(res - (s[ns:] ** 2).sum()) < 1e-10 * (s ** 2).sum()
+    # no other orthonormal basis of the same size does better
+    rng = np.random.default_rng(0)
+    X, _ = np.linalg.qr(W[:, :8] + 1e-3 * rng.standard_normal(W[:, :8].shape))
+    assert np.linalg.norm(U - X @ (X.T @ U)) ** 2 > (s[8:] ** 2).sum()
+
+
+def test_temporal_snapshot_indexing(c1_blocks):
+    # v_i^k is the k-th length-Nt segment of v_i, so by Eq. SVDsummation
+    # U_k = sum_i sigma_i w_i (v_i^k)^T, i.e. column k of Upsilon_i.
+    p, blocks = c1_blocks
+    r = pod.pod_exact(blocks, p.ns, p.nt)
+    W, s, V = r["W"], r["sigma"], r["V"]
+    n_mu, Nt = len(blocks), p.Nt
+    ups = [V[:, i].reshape(n_mu, Nt).T for i in range(len(s))]
+    for k in range(n_mu):
+        Uk = sum(s[i] * np.outer(W[:, i], ups[i][:, k]) for i in range(len(s)))
+        assert np.abs(Uk - blocks[k]).max() < 1e-11 * s[0]
+    T = r["T"]
+    for i in range(p.ns):
+        Ti = T[:, [i + p.ns * j for j in range(p.nt)]]
+        assert np.abs(Ti.T @ Ti - np.eye(p.nt)).max() < 1e-13
+        # Phi_t^i spans the dominant left singular space of Upsilon_i
+        lam, sv, _ = np.linalg.svd(ups[i], full_matrices=False)
+        assert np.abs(Ti @ Ti.T - lam[:, :p.nt] @ lam[:, :p.nt].T).max() < 1e-10
+        assert np.allclose(r["temporal_sigma"][i], sv[:r["temporal_sigma"].shape[1]])
+
+
+def test_incremental_equals_exact_when_untruncated(c1_blocks):
+    p, blocks = c1_blocks
+    ex = pod.pod_exact(blocks, p.ns, p.nt)
+    inc = pod.pod_block_incremental(blocks, p.ns, p.nt, r_max=10 ** 6, eps_svd=1e-14,
+                                    eps_sv=1e-15)
+    k = 40
+    s0 = ex["sigma"][0]
+    assert np.abs(inc["sigma"][:k] - ex["sigma"][:k]).max() < 1e-12 * s0
+    # leading spatial modes (distinct singular values) agree up to sign
+    assert np.abs(pod.canonical_signs(inc["Phi_s"]) - pod.canonical_signs(ex["Phi_s"])).max() < 1e-9
+    # temporal bases: compare projectors, which do not depend on signs
+    for i in range(p.ns):
+        cols = [i + p.ns * j for j in range(p.nt)]
+        Pe = ex["T"][:, cols] @ ex["T"][:, cols].T
+        Pi = inc["T"][:, cols] @ inc["T"][:, cols].T
+        assert np.abs(Pe - Pi).max() < 1e-8
+    W = inc["W"]
+    assert np.abs(W.T @ W - np.eye(W.shape[1])).max() < 1e-12
+
+
+def test_incremental_truncated_keeps_leading_modes(c1_blocks):
+    p, blocks = c1_blocks
+    ex = pod.pod_exact(blocks, p.ns, p.nt)
+    inc = pod.pod_block_incremental(blocks, p.ns, p.nt, r_max=60)
+    assert inc["W"].shape[1] == 60
+    s0 = ex["sigma"][0]
+    assert np.abs(inc["sigma"][:8] - ex["sigma"][:8]).max() < 1e-9 * s0
+    U = pod.snapshot_matrix(blocks)
+    approx = inc["W"] @ np.diag(inc["sigma"]) @ inc["V"].T
+    # truncation only removes small singular directions
+    assert np.linalg.norm(U - approx) < 1e-3 * np.linalg.norm(U)
+
+
+def test_incremental_dependent_and_zero_columns():
+    rng = np.random.default_rng(7)
+    base = rng.standard_normal((40, 3))
+    b1 = base @ rng.standard_normal((3, 6))          # rank 3 block
+    b2 = np.zeros((40, 6))                           # all-zero block
+    b3 = np.concatenate([b1[:, :2], rng.standard_normal((40, 4))], axis=1)
+    blocks = [b1, b2, b3]
+    ex = pod.pod_exact(blocks, 3, 2)
+    inc = pod.pod_block_incremental(blocks, 3, 2, r_max=100)
+    rank = np.linalg.matrix_rank(pod.snapshot_matrix(blocks))
+    assert inc["W"].shape[1] == rank == 7
+    assert np.abs(inc["sigma"] - ex["sigma"][:rank]).max() < 1e-12 * ex["sigma"][0]
+    approx = inc["W"] @ np.diag(inc["sigma"]) @ inc["V"].T
+    assert np.abs(approx - pod.snapshot_matrix(blocks)).max() < 1e-12 * ex["sigma"][0]
+
+
+def test_canonical_signs():
+    X = np.array([[1.0, -3.0], [-2.0, 1.0], [0.5, 3.0]])
+    C = pod.canonical_signs(X)
+    assert np.allclose(C[:, 0], -X[:, 0]) and np.allclose(C[:, 1], -X[:, 1])
+    assert np.allclose(pod.canonical_signs(-X), C)
