@@ -1,0 +1,222 @@
+/*
+ * st_rom.h -- C ABI of the GB300-native space-time reduced-order model for
+ * parametric linear dynamical systems (Choi, Brown, Arrighi, Anderson,
+ * "Space-time reduced order model for large-scale linear dynamical systems
+ * with application to Boltzmann transport problems").
+ *
+ * Problem (Sec. 2, Eq. Dynamicalstate):  du/dt = A(mu) u + B f(t), u(0) = u0,
+ * stepped by backward Euler (Eq. fom).  A(mu) is given in affine form
+ * A(mu) = sum_q theta_q A_q over Q sparse terms that share one pattern; the
+ * caller maps mu -> theta.
+ *
+ * Conventions used by every entry point:
+ *  - Dense matrices are column major (Fortran order).  "dev" pointers are
+ *    CUDA device pointers on the model's device; "host" pointers are ordinary
+ *    host memory.  The caller owns every pointer it passes; the library owns
+ *    the model handle and everything allocated inside it.
+ *  - Calls are enqueued on the model's stream and return before the GPU work
+ *    finishes, unless a call's comment says "synchronous".  Argument errors
+ *    are returned immediately (ST_ERR_ARG / ST_ERR_STATE) and nothing is
+ *    enqueued.  Errors detected on the device (non-convergence, breakdown,
+ *    zero pivot, non-finite values, a device wait that hit its limit) are
+ *    written to per-sample status arrays when the call takes one and to the
+ *    model's error word, which st_sync() returns and clears.
+ *  - Reduced unknowns are ordered i + ns*j (spatial mode i < ns fastest,
+ *    temporal mode j < nt), as in Eq. spacetimebasis.
+ *  - A model and its stream are used by one host thread at a time.
+ *  - st_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef ST_ROM_H
+#define ST_ROM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t st_status;
+#define ST_OK                0
+#define ST_ERR_ARG           1  /* invalid argument (checked on the host)           */
+#define ST_ERR_CUDA          2  /* a CUDA runtime call failed                       */
+#define ST_ERR_OOM           3  /* device allocation failed                         */
+#define ST_ERR_NOT_CONVERGED 4  /* iteration limit reached (BiCGSTAB, Jacobi SVD)   */
+#define ST_ERR_BREAKDOWN     5  /* BiCGSTAB breakdown (rho or omega vanished)       */
+#define ST_ERR_SINGULAR      6  /* zero pivot in the reduced LU factorisation       */
+#define ST_ERR_NONFINITE     7  /* NaN or Inf met in device arithmetic              */
+#define ST_ERR_TIMEOUT       8  /* a device-side wait exceeded options.spin_limit   */
+#define ST_ERR_STATE         9  /* call out of order (e.g. solve before assemble)   */
+
+/* Arithmetic of the reduced solve (st_options.precision). */
+#define ST_FP64          0  /* FP64 assembly, FP64 LU, FP64 refinement                 */
+#define ST_FP32_ASSEMBLY 1  /* FP32 assembly of Ahat^st, FP64 LU + FP64 refinement     */
+
+/* Opaque model handle: operator terms, bases, reduced operators, workspace. */
+typedef struct st_model st_model;
+
+/* Affine sparse operator, host CSR (Sec. 2; the transport operator of
+ * Sec. 6 is split into terms A_q).  All n_terms share rowptr/col. */
+typedef struct {
+    int64_t        n_rows;   /* N: spatial unknowns (square operator)            */
+    const int64_t* rowptr;   /* host [N + 1], rowptr[0] = 0, non-decreasing       */
+    const int32_t* col;      /* host [nnz], 0 <= col < N, unique within a row     */
+    const double* const* vals; /* host [n_terms] pointers to nnz values of A_q    */
+    int32_t        n_terms;  /* Q >= 1                                            */
+} st_affine_csr;
+
+typedef struct {
+    double  tol;          /* BiCGSTAB: stop at ||r|| <= tol * ||rhs||        (1e-13)  */
+    int32_t maxit;        /* BiCGSTAB iterations per time step               (1000)   */
+    double  eps_svd;      /* incremental SVD dependence test, relative to the
+                             largest column norm of the incoming block       (1e-12)  */
+    double  eps_sv;       /* drop singular values < eps_sv * sigma_max       (1e-14)  */
+    int32_t r_max;        /* rank cap of the incremental SVD                 (256)    */
+    int32_t precision;    /* ST_FP64 or ST_FP32_ASSEMBLY                     (FP64)   */
+    int64_t spin_limit;   /* polls of any device-side wait before it gives up
+                             with ST_ERR_TIMEOUT (one poll ~ 0.1 us)         (2e7)    */
+    int32_t refine_steps; /* iterative-refinement steps of the reduced solve (1)      */
+    int32_t jacobi_sweeps;/* sweep cap of the one-sided Jacobi SVD           (40)     */
+} st_options;
+
+/* Fill *opt with the defaults shown above. */
+void st_options_default(st_options* opt);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* st_last_error(void);
+
+/* Static name of a status code. */
+const char* st_status_string(st_status s);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * models, all devices); a diagnostic counter, never reset. */
+int64_t st_kernel_launches(void);
+
+/* Create a model on the current CUDA device.  Converts the host CSR terms to
+ * the library's sliced-ELL layout and uploads them (synchronous).
+ * stream: a cudaStream_t (NULL = the legacy default stream); the model keeps
+ * it for every later call.  opt may be NULL (defaults).  On success *out
+ * receives a handle that st_model_destroy releases.
+ * Errors: ST_ERR_ARG (bad CSR), ST_ERR_OOM, ST_ERR_CUDA. */
+st_status st_model_create(const st_affine_csr* A, const st_options* opt, void* stream,
+                          st_model** out);
+
+/* Release every resource of the model (synchronises its stream first). */
+void st_model_destroy(st_model* m);
+
+/* Wait for the model's stream, then return and clear the first device-side
+ * error recorded since the previous st_sync (ST_OK if none). */
+st_status st_sync(st_model* m);
+
+/* Full-order snapshot march (Eq. fom):
+ *   (I - dt_k A(mu_p)) u^k = u^{k-1} + dt_k B f^k,  k = 1..Nt, t_k = sum dt_j,
+ * for n_mu parameter samples marched together; each step is solved by
+ * BiCGSTAB (initial guess u^{k-1}) on the sliced-ELL operator, with all
+ * iteration control on the device.
+ *   theta     host [n_mu x Q] row major: theta_q(mu_p) at theta[p*Q + q]
+ *   dt        host [Nt] time steps
+ *   u0        dev  [N] initial state shared by all samples, or NULL for 0
+ *   B         dev  [N x n_in] input matrix; F host [Nt x n_in] row major, f^k
+ *             at F[(k-1)*n_in + s]  (n_in may be 0: no input)
+ *   snapshots dev  [N x (Nt*n_mu)]: column p*Nt + (k-1) receives u^k(mu_p),
+ *             i.e. U = [U_1 ... U_nmu] of Eq. snapshotmat
+ *   iters     dev  [Nt x n_mu] (or NULL): iterations of step k for sample p
+ *             at iters[(k-1)*n_mu + p]
+ *   status    dev  [n_mu] (or NULL): ST_OK, ST_ERR_NOT_CONVERGED,
+ *             ST_ERR_BREAKDOWN, ST_ERR_NONFINITE or ST_ERR_TIMEOUT per sample;
+ *             a failed sample stops marching, its later columns are zero.
+ * 1 <= n_mu (processed in groups of at most 32), 1 <= Nt. */
+st_status st_fom_march(st_model* m, int32_t n_mu, const double* theta, int32_t Nt,
+                       const double* dt, const double* u0, int32_t n_in, const double* B,
+                       const double* F, double* snapshots, int32_t* iters, int32_t* status);
+
+/* Spatial and temporal bases by the incremental POD of Secs. 4.1-4.2
+ * (synchronous).  The snapshot matrix U = [U_1 ... U_nmu] (N x Nt*n_mu,
+ * dev, column major, as written by st_fom_march) is consumed one parameter
+ * block U_p at a time: projection on the current left singular vectors W,
+ * column-wise Gram-Schmidt (two passes) of the remainder with the eps_svd
+ * dependence test, a second block pass (the new directions are projected on W
+ * again and re-orthogonalised), FP64 one-sided Jacobi SVD of the bordered
+ * middle matrix (Eq. middleMat), update of W, sigma, V (Eqs.
+ * rankOneUpdateSVD1-2), truncation by eps_sv and r_max.  Then
+ * Phi_s = W(:, 1:ns) (Eq. spatialincrementalbasis) and, for each i < ns, the
+ * temporal snapshot matrix Upsilon_i (Nt x n_mu) from the unscaled right
+ * singular vector v_i (Eq. incrementaltemporalsnapshotmat) and its SVD give
+ * Phi_t^i = Lambda_i(:, 1:nt) (Eq. temporalincrementalbasis).
+ *   sigma  host [r_max] or NULL: singular values, descending, rank entries set
+ *   rank   host or NULL: number of singular triplets kept (r)
+ * Requires ns <= r and nt <= min(Nt, n_mu); ST_ERR_ARG otherwise.
+ * Replaces any basis or reduced operators held by the model. */
+st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt, const double* snapshots,
+                             int32_t ns, int32_t nt, double* sigma, int32_t* rank);
+
+/* Install caller-provided bases (e.g. to assemble from another POD).
+ * phi_s dev [N x ns]; T dev [Nt x ns*nt] with column i + ns*j = phi_t^{i,j}
+ * (Eq. spacetimebasisvec).  Copies them (asynchronous).  Clears reduced ops. */
+st_status st_model_set_basis(st_model* m, int32_t ns, int32_t nt, int32_t Nt,
+                             const double* phi_s, const double* T);
+
+/* Copy the bases out.  phi_s dev [N x ns] or NULL, T dev [Nt x ns*nt] or
+ * NULL; dims host [3] or NULL receives (ns, nt, Nt). */
+st_status st_model_get_basis(st_model* m, double* phi_s, double* T, int32_t* dims);
+
+/* Incremental-SVD state after st_rom_build_basis (synchronous copy):
+ * W dev [N x r] or NULL, V dev [(Nt*n_mu) x r] or NULL, sigma host [r] or
+ * NULL, r host or NULL. */
+st_status st_pod_get_state(st_model* m, double* W, double* V, double* sigma, int32_t* r);
+
+/* Offline assembly of the space-time reduced operators through the block
+ * structure of Sec. 4.3, never forming Phi_st:
+ *   Ahat_q = Phi_s^T A_q Phi_s           (reduced system matrix, Eq. galerkin)
+ *   G[(i',j'),(i,j)] = sum_k dt_k phi_{i'j'}[k] phi_{ij}[k]
+ *   M_i[j',j] = sum_k phi_{ij'}[k] phi_{ij}[k]
+ *   S_i[j',j] = sum_{k<Nt} phi_{ij'}[k+1] phi_{ij}[k]    (Eq. ij-block-matrix)
+ *   fhat^st block j = sum_k dt_k D_k^j Phi_s^T B f^k     (Eq. j-block-vector)
+ *   uhat0^st block j = D_1^j Phi_s^T u0  (Phi_st^T u0^st from Eq. ststate)
+ * dt host [Nt]; B dev [N x n_in]; F host [Nt x n_in] row major; u0 dev [N]
+ * or NULL.  Requires a basis.  Asynchronous. */
+st_status st_rom_assemble(st_model* m, const double* dt, int32_t n_in, const double* B,
+                          const double* F, const double* u0);
+
+/* Copy the assembled reduced operators to host memory (synchronous); any
+ * pointer may be NULL.  Ahat [Q x ns x ns] (term q at Ahat + q*ns*ns, column
+ * major), G [n x n], M and S [ns x nt x nt] (mode i at + i*nt*nt, column
+ * major), rhs [n] = fhat^st + uhat0^st, with n = ns*nt. */
+st_status st_model_get_reduced(st_model* m, double* Ahat, double* G, double* M, double* S,
+                               double* rhs);
+
+/* Batched online solve of the space-time Galerkin system (Eq. st-galerkin)
+ *   Ahat^st(mu) uhat = fhat^st + uhat0^st
+ * with Ahat^st[(i',j'),(i,j)] = delta_{i'i} (M_i - S_i)[j',j]
+ *                              - Ahat(mu)[i',i] G[(i',j'),(i,j)],
+ * Ahat(mu) = sum_q theta_q Ahat_q, for n_mu samples with individual nested
+ * sizes (ns_p <= ns, nt_p <= nt; the sub-basis i < ns_p, j < nt_p).  One
+ * persistent kernel assembles, LU-factorises with partial pivoting (FP64),
+ * solves and refines each sample, largest first.
+ *   theta   dev [n_mu x Q] row major
+ *   ns_nt   dev [n_mu x 2] (ns_p, nt_p) or NULL for the model's (ns, nt)
+ *   uhat    dev [n_mu x ns*nt]: sample p writes its ns_p*nt_p coefficients,
+ *           ordered i + ns_p*j, at uhat + p*ns*nt
+ *   rel_res dev [n_mu] or NULL: ||rhs - Ahat^st uhat|| / ||rhs|| after refinement
+ *   status  dev [n_mu] or NULL: ST_OK, ST_ERR_SINGULAR, ST_ERR_NONFINITE
+ * Asynchronous; repeated calls reuse the model's workspace. */
+st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta, const int32_t* ns_nt,
+                       double* uhat, double* rel_res, int32_t* status);
+
+/* Reconstruction u^st ~= Phi_st uhat (Eq. ststateapproximation) by blocks:
+ *   C[i,k] = sum_j uhat[i + ns_p j] phi_t^{i,j}[k],  u^k = Phi_s C[:,k].
+ *   uhat  dev [n_mu x ns*nt] as written by st_rom_solve; ns_nt as there
+ *   u     dev [N x Nt x n_mu] or NULL: full fields, u^k(mu_p) in column
+ *         p*Nt + (k-1)
+ *   Cout  dev [N x n_out] or NULL; y dev [n_out x Nt x n_mu] or NULL: outputs
+ *         y^k = Cout^T u^k (Eq. Dynamicaloutput) computed through
+ *         Chat = Phi_s^T Cout without forming u (Eq. outputFromReducedsol).
+ * Asynchronous. */
+st_status st_rom_reconstruct(st_model* m, int32_t n_mu, const double* uhat,
+                             const int32_t* ns_nt, double* u, int32_t n_out, const double* Cout,
+                             double* y);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_ROM_H */

@@ -13,13 +13,17 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 * ``pod_block_incremental`` -- the incremental SVD of Sec. 4.2 (Eqs.
   factorization1 ... rankOneUpdateSVD2, Algorithms 1-2), taking one
   parameter's Nt snapshots per update:
-    1. project the block on W twice (classical Gram-Schmidt, two passes):
-       L = W^T U_p, E = U_p - W L, then once more on E;
-    2. within the block, column by column, project each column of E on the
-       new directions J found so far (two passes), and keep its normalised
+    1. project the block on W: L1 = W^T U_p, E1 = U_p - W L1;
+    2. within the block, column by column, project each column of E1 on the
+       new directions found so far (two passes), and keep its normalised
        remainder as a new direction unless its norm is below the dependence
        threshold (the "p < eps_SVD" test of Algorithm 2, read relative to the
-       block's largest column norm); this gives E = J P;
+       block's largest column norm); this gives E1 = J1 P1;
+    2b. second block pass, the finite-precision safeguard of Sec. 4.2 taken
+       as block Gram-Schmidt twice: a remainder normalised from a small norm
+       amplifies its rounding along W, so J1 is projected on W again,
+       L2 = W^T J1, and J1 - W L2 = J P2 is re-orthogonalised; then
+       U_p = W L + J P with L = L1 + L2 P1 and P = P2 P1;
     3. SVD of the bordered middle matrix Q = [[diag(sigma), L], [0, P]]
        (Eq. middleMat, with a block border instead of one column);
     4. W <- [W J] Ubar, sigma <- diag(Sigma_bar), V <- blkdiag(V, I) Vbar
@@ -105,15 +109,20 @@ def incremental_update(W: Optional[np.ndarray], sigma: Optional[np.ndarray],
     tau = eps_svd * float(np.max(np.linalg.norm(Up, axis=0))) if m else 0.0
     r = 0 if W is None else W.shape[1]
     if r > 0:
-        L = W.T @ Up
-        E = Up - W @ L
-        L2 = W.T @ E
-        E = E - W @ L2
-        L = L + L2
+        # first block pass: project on W, orthogonalise the remainder
+        L1 = W.T @ Up
+        E1 = Up - W @ L1
+        J1, P1 = _colwise_gs2(E1, tau)
+        # second block pass: directions of E1 that were normalised from a
+        # small remainder carry amplified rounding along W; project J1 on W
+        # again and re-orthogonalise (U_p = W (L1 + L2 P1) + J (P2 P1))
+        L2 = W.T @ J1
+        J, P2 = _colwise_gs2(J1 - W @ L2, 0.0)
+        L = L1 + L2 @ P1
+        P = P2 @ P1
     else:
         L = np.zeros((0, m))
-        E = Up.copy()
-    J, P = _colwise_gs2(E, tau)
+        J, P = _colwise_gs2(Up.copy(), tau)
     k = J.shape[1]
     Qm = np.zeros((r + k, r + m), dtype=np.float64)
     if r > 0:

@@ -1,0 +1,215 @@
+"""ctypes binding of libst_rom.so (the C ABI declared in include/st_rom.h).
+
+Argument marshalling only: every step of the method runs inside the CUDA
+library.  Device buffers are passed as anything with ``data_ptr()`` (torch
+tensors) or as raw integer addresses; host arrays are numpy arrays.  Every
+function has the C name; a non-zero status raises ``StError`` carrying the
+library's message.  If the library has not been built the import fails: there
+is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libst_rom.so")
+
+ST_OK = 0
+ST_ERR_ARG = 1
+ST_ERR_CUDA = 2
+ST_ERR_OOM = 3
+ST_ERR_NOT_CONVERGED = 4
+ST_ERR_BREAKDOWN = 5
+ST_ERR_SINGULAR = 6
+ST_ERR_NONFINITE = 7
+ST_ERR_TIMEOUT = 8
+ST_ERR_STATE = 9
+ST_FP64 = 0
+ST_FP32_ASSEMBLY = 1
+
+
+class StError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{code}: {msg}")
+        self.code = code
+
+
+class st_options(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("maxit", c_int32), ("eps_svd", c_double),
+                ("eps_sv", c_double), ("r_max", c_int32), ("precision", c_int32),
+                ("spin_limit", c_int64), ("refine_steps", c_int32), ("jacobi_sweeps", c_int32)]
+
+
+class st_affine_csr(ctypes.Structure):
+    _fields_ = [("n_rows", c_int64), ("rowptr", POINTER(c_int64)), ("col", POINTER(c_int32)),
+                ("vals", POINTER(POINTER(c_double))), ("n_terms", c_int32)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+lib = ctypes.CDLL(LIB_PATH)
+
+_P = c_void_p
+_SIGS = {
+    "st_options_default": (None, [POINTER(st_options)]),
+    "st_last_error": (c_char_p, []),
+    "st_status_string": (c_char_p, [c_int32]),
+    "st_kernel_launches": (c_int64, []),
+    "st_model_create": (c_int32, [POINTER(st_affine_csr), POINTER(st_options), _P, POINTER(_P)]),
+    "st_model_destroy": (None, [_P]),
+    "st_sync": (c_int32, [_P]),
+    "st_fom_march": (c_int32, [_P, c_int32, _P, c_int32, _P, _P, c_int32, _P, _P, _P, _P, _P]),
+    "st_rom_build_basis": (c_int32, [_P, c_int32, c_int32, _P, c_int32, c_int32, _P, _P]),
+    "st_model_set_basis": (c_int32, [_P, c_int32, c_int32, c_int32, _P, _P]),
+    "st_model_get_basis": (c_int32, [_P, _P, _P, _P]),
+    "st_pod_get_state": (c_int32, [_P, _P, _P, _P, _P]),
+    "st_rom_assemble": (c_int32, [_P, _P, c_int32, _P, _P, _P]),
+    "st_model_get_reduced": (c_int32, [_P, _P, _P, _P, _P, _P]),
+    "st_rom_solve": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
+    "st_rom_reconstruct": (c_int32, [_P, c_int32, _P, _P, _P, c_int32, _P, _P]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def ptr(x) -> int | None:
+    """Address of a device tensor, host numpy array or raw integer (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _host(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def last_error() -> str:
+    return lib.st_last_error().decode()
+
+
+def check(code: int) -> None:
+    if code != ST_OK:
+        raise StError(code, last_error())
+
+
+def options(**kw) -> st_options:
+    o = st_options()
+    lib.st_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Model:
+    """Owner of one st_model handle; methods are the C entry points with the
+    model argument bound.  Host inputs are converted to contiguous arrays."""
+
+    def __init__(self, rowptr, col, vals, opts: st_options | None = None, stream=None):
+        self._rowptr = _host(rowptr, np.int64)
+        self._col = _host(col, np.int32)
+        vals = np.asarray(vals, dtype=np.float64)
+        if vals.ndim == 1:
+            vals = vals[None]
+        self._vals = [np.ascontiguousarray(v) for v in vals]
+        arr = (POINTER(c_double) * len(self._vals))(
+            *[v.ctypes.data_as(POINTER(c_double)) for v in self._vals])
+        self._csr = st_affine_csr(self._rowptr.shape[0] - 1,
+                                  self._rowptr.ctypes.data_as(POINTER(c_int64)),
+                                  self._col.ctypes.data_as(POINTER(c_int32)),
+                                  ctypes.cast(arr, POINTER(POINTER(c_double))), len(self._vals))
+        self._arr = arr
+        self.opts = opts if opts is not None else options()
+        h = c_void_p()
+        st = stream if stream is None or isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
+        check(lib.st_model_create(ctypes.byref(self._csr), ctypes.byref(self.opts), st,
+                                  ctypes.byref(h)))
+        self.handle = h
+        self.N = int(self._rowptr.shape[0] - 1)
+        self.Q = len(self._vals)
+        self._keep = []
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib.st_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C entry points ---------------------------------------------------
+    def st_sync(self) -> None:
+        check(lib.st_sync(self.handle))
+
+    def st_fom_march(self, theta, dt, u0, B, F, snapshots, iters=None, status=None) -> None:
+        th = _host(theta, np.float64)
+        dth = _host(dt, np.float64)
+        Fh = _host(F, np.float64) if F is not None else None
+        n_in = 0 if Fh is None else (Fh.shape[1] if Fh.ndim == 2 else 1)
+        self._keep = [th, dth, Fh]
+        check(lib.st_fom_march(self.handle, th.shape[0], ptr(th), dth.shape[0], ptr(dth), ptr(u0),
+                               n_in, ptr(B), ptr(Fh), ptr(snapshots), ptr(iters), ptr(status)))
+
+    def st_rom_build_basis(self, n_mu, Nt, snapshots, ns, nt):
+        sig = np.zeros(max(int(self.opts.r_max), 1), dtype=np.float64)
+        rank = np.zeros(1, dtype=np.int32)
+        check(lib.st_rom_build_basis(self.handle, n_mu, Nt, ptr(snapshots), ns, nt, ptr(sig),
+                                     ptr(rank)))
+        return sig[:rank[0]].copy(), int(rank[0])
+
+    def st_model_set_basis(self, ns, nt, Nt, phi_s, T) -> None:
+        check(lib.st_model_set_basis(self.handle, ns, nt, Nt, ptr(phi_s), ptr(T)))
+
+    def st_model_get_basis(self, phi_s=None, T=None):
+        dims = np.zeros(3, dtype=np.int32)
+        check(lib.st_model_get_basis(self.handle, ptr(phi_s), ptr(T), ptr(dims)))
+        return tuple(int(d) for d in dims)
+
+    def st_pod_get_state(self, W=None, V=None):
+        r = np.zeros(1, dtype=np.int32)
+        check(lib.st_pod_get_state(self.handle, None, None, None, ptr(r)))
+        sig = np.zeros(max(int(r[0]), 1), dtype=np.float64)
+        check(lib.st_pod_get_state(self.handle, ptr(W), ptr(V), ptr(sig), ptr(r)))
+        return sig[:r[0]].copy(), int(r[0])
+
+    def st_rom_assemble(self, dt, B, F, u0=None) -> None:
+        dth = _host(dt, np.float64)
+        Fh = _host(F, np.float64) if F is not None else None
+        n_in = 0 if Fh is None else (Fh.shape[1] if Fh.ndim == 2 else 1)
+        self._keep = [dth, Fh]
+        check(lib.st_rom_assemble(self.handle, ptr(dth), n_in, ptr(B), ptr(Fh), ptr(u0)))
+
+    def st_model_get_reduced(self, ns, nt):
+        n = ns * nt
+        Ahat = np.zeros((self.Q, ns, ns))
+        G = np.zeros((n, n))
+        M = np.zeros((ns, nt, nt))
+        S = np.zeros((ns, nt, nt))
+        rhs = np.zeros(n)
+        check(lib.st_model_get_reduced(self.handle, ptr(Ahat), ptr(G), ptr(M), ptr(S), ptr(rhs)))
+        # library layout is column major per matrix
+        return (Ahat.transpose(0, 2, 1).copy(), G.T.copy(), M.transpose(0, 2, 1).copy(),
+                S.transpose(0, 2, 1).copy(), rhs)
+
+    def st_rom_solve(self, n_mu, theta, ns_nt, uhat, rel_res=None, status=None) -> None:
+        check(lib.st_rom_solve(self.handle, n_mu, ptr(theta), ptr(ns_nt), ptr(uhat), ptr(rel_res),
+                               ptr(status)))
+
+    def st_rom_reconstruct(self, n_mu, uhat, ns_nt, u=None, n_out=0, Cout=None, y=None) -> None:
+        check(lib.st_rom_reconstruct(self.handle, n_mu, ptr(uhat), ptr(ns_nt), ptr(u), n_out,
+                                     ptr(Cout), ptr(y)))

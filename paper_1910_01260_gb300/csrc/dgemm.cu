@@ -1,0 +1,157 @@
+// FP64 SIMT GEMM, column major, batched, with a deterministic split over K.
+//
+// GB300 issues FP64 at a small fraction of its FP32 rate, so a register tile
+// of 4x4 outputs per thread and a 64x64x16 shared-memory tile already keep
+// the FP64 pipe busy; the kernel's job is to avoid redundant global traffic
+// and to expose enough tiles (split-K) for the tall-skinny products of the
+// POD, where K is the number of spatial unknowns.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(NT) dgemm_kernel(int64_t M, int64_t Nc, int64_t K, int64_t kchunk,
+                                                   double alpha, const double* __restrict__ A,
+                                                   int64_t lda, int64_t sA, const double* __restrict__ B,
+                                                   int64_t ldb, int64_t sB, double beta, double* C,
+                                                   int64_t ldc, int64_t sC, int splits, double* ws) {
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
+    const int bz = blockIdx.z;
+    const int batch = bz / splits, split = bz % splits;
+    A += batch * sA;
+    B += batch * sB;
+    C += batch * sC;
+    const int64_t kb = (int64_t)split * kchunk;
+    const int64_t ke = K < kb + kchunk ? K : kb + kchunk;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+        // A tile: BM x BK
+#pragma unroll
+        for (int l = 0; l < (BM * BK) / NT; ++l) {
+            int idx = tid + l * NT;
+            int ii, kk;
+            if (!TA) { ii = idx % BM; kk = idx / BM; }
+            else     { kk = idx % BK; ii = idx / BK; }
+            int64_t gi = i0 + ii, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < M && gk < ke) v = TA ? A[gk + gi * lda] : A[gi + gk * lda];
+            As[kk][ii] = v;
+        }
+        // B tile: BK x BN
+#pragma unroll
+        for (int l = 0; l < (BN * BK) / NT; ++l) {
+            int idx = tid + l * NT;
+            int jj, kk;
+            if (!TB) { kk = idx % BK; jj = idx / BK; }
+            else     { jj = idx % BN; kk = idx / BN; }
+            int64_t gj = j0 + jj, gk = k0 + kk;
+            double v = 0.0;
+            if (gj < Nc && gk < ke) v = TB ? B[gj + gk * ldb] : B[gk + gj * ldb];
+            Bs[kk][jj] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                a[t] = As[kk][tx + 16 * t];
+                b[t] = Bs[kk][ty + 16 * t];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        int64_t gi = i0 + tx + 16 * x;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            int64_t gj = j0 + ty + 16 * y;
+            if (gj >= Nc) continue;
+            if (splits == 1) {
+                double* c = C + gi + gj * ldc;
+                *c = beta == 0.0 ? alpha * acc[x][y] : fma(alpha, acc[x][y], beta * *c);
+            } else {
+                ws[(size_t)split * M * Nc + gi + gj * M] = acc[x][y];
+            }
+        }
+    }
+}
+
+__global__ void splitk_reduce(int64_t M, int64_t Nc, int splits, const double* __restrict__ ws,
+                              double alpha, double beta, double* C, int64_t ldc) {
+    int64_t n = M * Nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int p = 0; p < splits; ++p) s += ws[(size_t)p * n + t];
+        int64_t i = t % M, j = t / M;
+        double* c = C + i + j * ldc;
+        *c = beta == 0.0 ? alpha * s : fma(alpha, s, beta * *c);
+    }
+}
+
+}  // namespace
+
+st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nc, int64_t K,
+                   double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                   double beta, double* C, int64_t ldc, int batch, int64_t sA, int64_t sB,
+                   int64_t sC) {
+    if (M <= 0 || Nc <= 0 || batch <= 0) return ST_OK;
+    if (K <= 0) {
+        // C = beta * C
+        if (beta == 1.0) return ST_OK;
+        K = 0;
+    }
+    int64_t tiles = ((M + BM - 1) / BM) * ((Nc + BN - 1) / BN) * batch;
+    int splits = 1;
+    if (batch == 1 && K > 2048 && tiles < 2 * m->num_sms) {
+        int64_t want = (2 * m->num_sms + tiles - 1) / tiles;
+        want = std::min<int64_t>(want, K / 512);
+        splits = (int)std::max<int64_t>(1, std::min<int64_t>(want, 64));
+    }
+    int64_t kchunk = K > 0 ? ((K + splits - 1) / splits + BK - 1) / BK * BK : 0;
+    if (K > 0) splits = (int)((K + kchunk - 1) / kchunk);
+    double* ws = nullptr;
+    if (splits > 1) {
+        ST_TRY(st_grow(m, m->ws_gemm, sizeof(double) * (size_t)splits * M * Nc));
+        ws = (double*)m->ws_gemm.p;
+    }
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((Nc + BN - 1) / BN),
+              (unsigned)(batch * std::max(splits, 1)));
+    if (grid.y > 65535 || grid.z > 65535) return st_fail(ST_ERR_ARG, "st_dgemm: grid too large");
+    int sp = std::max(splits, 1);
+#define ST_LAUNCH(ta, tb)                                                                   \
+    dgemm_kernel<ta, tb><<<grid, NT, 0, m->stream>>>(M, Nc, K, kchunk, alpha, A, lda, sA, B, \
+                                                     ldb, sB, beta, C, ldc, sC, sp, ws)
+    if (!transA && !transB) ST_LAUNCH(false, false);
+    else if (transA && !transB) ST_LAUNCH(true, false);
+    else if (!transA && transB) ST_LAUNCH(false, true);
+    else ST_LAUNCH(true, true);
+#undef ST_LAUNCH
+    ST_TRY(st_check_launch("dgemm"));
+    if (splits > 1) {
+        int blocks = (int)std::min<int64_t>((M * Nc + 255) / 256, 4 * m->num_sms);
+        splitk_reduce<<<blocks, 256, 0, m->stream>>>(M, Nc, splits, ws, alpha, beta, C, ldc);
+        ST_TRY(st_check_launch("splitk_reduce"));
+    }
+    return ST_OK;
+}

@@ -1,0 +1,114 @@
+// Internal declarations shared by the translation units of libst_rom.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "st_rom.h"
+
+// Slice height of the sliced-ELL layout (one warp-row group per slice).
+constexpr int kSlice = 32;
+
+// Growable device buffer owned by a model.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct st_model {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    st_options opt{};
+    int num_sms = 0;
+
+    // affine operator terms in sliced-ELL form
+    int64_t N = 0, nnz = 0;
+    int Q = 0;
+    int64_t n_slices = 0, ell_size = 0;
+    int max_width = 0;
+    int64_t* d_slice_ptr = nullptr;  // [n_slices + 1] entry offsets
+    int32_t* d_slice_w = nullptr;    // [n_slices] widths
+    int32_t* d_col = nullptr;        // [ell_size]
+    double* d_vals = nullptr;        // [Q * ell_size]
+
+    // bases
+    int ns = 0, nt = 0, Nt = 0;
+    double* d_phi = nullptr;  // N x ns
+    double* d_T = nullptr;    // Nt x ns*nt
+
+    // incremental SVD state
+    int pod_r = 0;
+    int64_t pod_rows = 0;
+    DevBuf W, V;
+    std::vector<double> sigma;
+
+    // reduced operators
+    bool assembled = false;
+    double* d_Ahat = nullptr;  // Q x ns x ns
+    double* d_G = nullptr;     // n x n
+    float* d_G32 = nullptr;    // n x n (FP32 copy for the FP32 assembly mode)
+    double* d_M = nullptr;     // ns x nt x nt
+    double* d_S = nullptr;     // ns x nt x nt
+    double* d_rhs = nullptr;   // n: fhat^st + uhat0^st
+    double* d_dt = nullptr;    // Nt
+
+    // device error word and barrier counters
+    int32_t* d_err = nullptr;
+    unsigned int* d_bar = nullptr;  // [4]: arrival count, generation, abort flag, queue head
+
+    // scratch buffers (grown on demand, reused across calls)
+    DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_solve, ws_misc;
+};
+
+// ---- error handling -------------------------------------------------------
+void st_set_error(const char* fmt, ...);
+st_status st_fail(st_status code, const char* fmt, ...);
+
+#define ST_CUDA_TRY(call)                                                              \
+    do {                                                                               \
+        cudaError_t e__ = (call);                                                      \
+        if (e__ != cudaSuccess)                                                        \
+            return st_fail(e__ == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA, \
+                           "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e__),      \
+                           __FILE__, __LINE__);                                        \
+    } while (0)
+
+#define ST_TRY(expr)                  \
+    do {                              \
+        st_status s__ = (expr);       \
+        if (s__ != ST_OK) return s__; \
+    } while (0)
+
+// Make sure buf holds at least `bytes`; synchronises the model stream before
+// releasing a smaller buffer that queued work may still use.
+st_status st_grow(st_model* m, DevBuf& buf, size_t bytes);
+st_status st_check_launch(const char* what);
+// Count one kernel launch (st_check_launch counts the launch it checks).
+void st_count_launch();
+
+// Number of co-resident blocks for a cooperative launch of `kernel`.
+template <typename K>
+int st_coop_blocks(st_model* m, K kernel, int threads, size_t smem, int per_sm_cap) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+        return 0;
+    if (per_sm > per_sm_cap) per_sm = per_sm_cap;
+    return per_sm * m->num_sms;
+}
+
+// ---- FP64 GEMM (column major): C = alpha * op(A) * op(B) + beta * C -------
+// Batched with element strides sA, sB, sC.  For long K the product is split
+// over K into a workspace and reduced in a fixed order (deterministic).
+st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Ncols, int64_t K,
+                   double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                   double beta, double* C, int64_t ldc, int batch = 1, int64_t sA = 0,
+                   int64_t sB = 0, int64_t sC = 0);
+
+// Release basis (and reduced operators) / reduced operators only.
+void st_internal_free_basis(st_model* m);
+void st_internal_free_reduced(st_model* m);

@@ -1,0 +1,315 @@
+// Model lifecycle, options, errors, sliced-ELL conversion and accessors.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+#include <atomic>
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void st_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void st_set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+st_status st_fail(st_status code, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+st_status st_grow(st_model* m, DevBuf& buf, size_t bytes) {
+    if (bytes <= buf.bytes) return ST_OK;
+    if (buf.p) {
+        ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        ST_CUDA_TRY(cudaFree(buf.p));
+        buf.p = nullptr;
+        buf.bytes = 0;
+    }
+    size_t want = bytes + bytes / 8 + 256;
+    ST_CUDA_TRY(cudaMalloc(&buf.p, want));
+    buf.bytes = want;
+    return ST_OK;
+}
+
+st_status st_check_launch(const char* what) {
+    st_count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return st_fail(ST_ERR_CUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    return ST_OK;
+}
+
+extern "C" {
+
+void st_options_default(st_options* o) {
+    if (!o) return;
+    o->tol = 1e-13;
+    o->maxit = 1000;
+    o->eps_svd = 1e-12;
+    o->eps_sv = 1e-14;
+    o->r_max = 256;
+    o->precision = ST_FP64;
+    o->spin_limit = 20000000LL;
+    o->refine_steps = 1;
+    o->jacobi_sweeps = 40;
+}
+
+const char* st_last_error(void) { return g_last_error.c_str(); }
+
+int64_t st_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* st_status_string(st_status s) {
+    switch (s) {
+        case ST_OK: return "ST_OK";
+        case ST_ERR_ARG: return "ST_ERR_ARG";
+        case ST_ERR_CUDA: return "ST_ERR_CUDA";
+        case ST_ERR_OOM: return "ST_ERR_OOM";
+        case ST_ERR_NOT_CONVERGED: return "ST_ERR_NOT_CONVERGED";
+        case ST_ERR_BREAKDOWN: return "ST_ERR_BREAKDOWN";
+        case ST_ERR_SINGULAR: return "ST_ERR_SINGULAR";
+        case ST_ERR_NONFINITE: return "ST_ERR_NONFINITE";
+        case ST_ERR_TIMEOUT: return "ST_ERR_TIMEOUT";
+        case ST_ERR_STATE: return "ST_ERR_STATE";
+        default: return "ST_ERR_UNKNOWN";
+    }
+}
+
+static void free_basis(st_model* m) {
+    cudaFree(m->d_phi);
+    cudaFree(m->d_T);
+    m->d_phi = m->d_T = nullptr;
+    m->ns = m->nt = m->Nt = 0;
+}
+
+static void free_reduced(st_model* m) {
+    cudaFree(m->d_Ahat);
+    cudaFree(m->d_G);
+    cudaFree(m->d_G32);
+    cudaFree(m->d_M);
+    cudaFree(m->d_S);
+    cudaFree(m->d_rhs);
+    cudaFree(m->d_dt);
+    m->d_Ahat = m->d_G = m->d_M = m->d_S = m->d_rhs = m->d_dt = nullptr;
+    m->d_G32 = nullptr;
+    m->assembled = false;
+}
+
+void st_model_destroy(st_model* m) {
+    if (!m) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(m->device);
+    cudaStreamSynchronize(m->stream);
+    free_basis(m);
+    free_reduced(m);
+    cudaFree(m->d_slice_ptr);
+    cudaFree(m->d_slice_w);
+    cudaFree(m->d_col);
+    cudaFree(m->d_vals);
+    cudaFree(m->d_err);
+    cudaFree(m->d_bar);
+    for (DevBuf* b : {&m->W, &m->V, &m->ws_fom, &m->ws_pod, &m->ws_pod2, &m->ws_gemm,
+                      &m->ws_solve, &m->ws_misc})
+        cudaFree(b->p);
+    cudaSetDevice(cur);
+    delete m;
+}
+
+st_status st_model_create(const st_affine_csr* A, const st_options* opt, void* stream,
+                          st_model** out) {
+    if (!A || !out) return st_fail(ST_ERR_ARG, "st_model_create: NULL argument");
+    *out = nullptr;
+    const int64_t N = A->n_rows;
+    if (N <= 0 || N > (int64_t)INT32_MAX) return st_fail(ST_ERR_ARG, "n_rows out of range");
+    if (A->n_terms < 1 || A->n_terms > 16) return st_fail(ST_ERR_ARG, "n_terms must be in [1,16]");
+    if (!A->rowptr || !A->col || !A->vals) return st_fail(ST_ERR_ARG, "NULL CSR array");
+    if (A->rowptr[0] != 0) return st_fail(ST_ERR_ARG, "rowptr[0] must be 0");
+    for (int q = 0; q < A->n_terms; ++q)
+        if (!A->vals[q]) return st_fail(ST_ERR_ARG, "NULL value array for term %d", q);
+    const int64_t nnz = A->rowptr[N];
+    int max_w = 0;
+    for (int64_t r = 0; r < N; ++r) {
+        int64_t len = A->rowptr[r + 1] - A->rowptr[r];
+        if (len < 0) return st_fail(ST_ERR_ARG, "rowptr decreases at row %lld", (long long)r);
+        if (len > 4096) return st_fail(ST_ERR_ARG, "row %lld has more than 4096 entries", (long long)r);
+        max_w = std::max(max_w, (int)len);
+    }
+    for (int64_t e = 0; e < nnz; ++e)
+        if (A->col[e] < 0 || A->col[e] >= N)
+            return st_fail(ST_ERR_ARG, "column index out of range at entry %lld", (long long)e);
+    st_options o;
+    st_options_default(&o);
+    if (opt) o = *opt;
+    if (!(o.tol > 0) || o.maxit < 1 || o.r_max < 1 || !(o.eps_svd >= 0) || !(o.eps_sv >= 0) ||
+        o.spin_limit < 1 || o.refine_steps < 0 || o.jacobi_sweeps < 1 ||
+        (o.precision != ST_FP64 && o.precision != ST_FP32_ASSEMBLY))
+        return st_fail(ST_ERR_ARG, "invalid st_options");
+
+    st_model* m = new st_model();
+    m->opt = o;
+    m->stream = (cudaStream_t)stream;
+    m->N = N;
+    m->nnz = nnz;
+    m->Q = A->n_terms;
+    if (cudaGetDevice(&m->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess) {
+        delete m;
+        return st_fail(ST_ERR_CUDA, "no CUDA device available");
+    }
+    // sliced-ELL: slices of kSlice consecutive rows; entry (k, lane) of
+    // slice s at slice_ptr[s] + k * kSlice + lane; padding has value 0 and
+    // points at the row itself.
+    const int64_t ns_ = (N + kSlice - 1) / kSlice;
+    std::vector<int64_t> sptr(ns_ + 1, 0);
+    std::vector<int32_t> sw(ns_, 0);
+    for (int64_t s = 0; s < ns_; ++s) {
+        int w = 0;
+        for (int64_t r = s * kSlice; r < std::min<int64_t>(N, (s + 1) * kSlice); ++r)
+            w = std::max<int>(w, (int)(A->rowptr[r + 1] - A->rowptr[r]));
+        sw[s] = w;
+        sptr[s + 1] = sptr[s] + (int64_t)w * kSlice;
+    }
+    const int64_t ell = sptr[ns_];
+    std::vector<int32_t> col(ell);
+    std::vector<double> vals((size_t)m->Q * ell, 0.0);
+    for (int64_t s = 0; s < ns_; ++s) {
+        for (int lane = 0; lane < kSlice; ++lane) {
+            int64_t r = s * kSlice + lane;
+            int64_t b = r < N ? A->rowptr[r] : 0, len = r < N ? A->rowptr[r + 1] - b : 0;
+            for (int k = 0; k < sw[s]; ++k) {
+                int64_t e = sptr[s] + (int64_t)k * kSlice + lane;
+                if (k < len) {
+                    col[e] = A->col[b + k];
+                    for (int q = 0; q < m->Q; ++q) vals[(size_t)q * ell + e] = A->vals[q][b + k];
+                } else {
+                    col[e] = r < N ? (int32_t)r : 0;
+                }
+            }
+        }
+    }
+    m->n_slices = ns_;
+    m->ell_size = ell;
+    m->max_width = max_w;
+    auto fail = [&](cudaError_t e) {
+        st_model_destroy(m);
+        return st_fail(e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA,
+                       "st_model_create: %s", cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&m->d_slice_ptr, sizeof(int64_t) * (ns_ + 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&m->d_slice_w, sizeof(int32_t) * ns_)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&m->d_col, sizeof(int32_t) * std::max<int64_t>(ell, 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&m->d_vals, sizeof(double) * m->Q * std::max<int64_t>(ell, 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&m->d_err, sizeof(int32_t))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&m->d_bar, sizeof(unsigned int) * 4)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(m->d_slice_ptr, sptr.data(), sizeof(int64_t) * (ns_ + 1), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(m->d_slice_w, sw.data(), sizeof(int32_t) * ns_, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if (ell > 0) {
+        if ((e = cudaMemcpy(m->d_col, col.data(), sizeof(int32_t) * ell, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(m->d_vals, vals.data(), sizeof(double) * m->Q * ell, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    }
+    if ((e = cudaMemset(m->d_err, 0, sizeof(int32_t))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(m->d_bar, 0, sizeof(unsigned int) * 4)) != cudaSuccess) return fail(e);
+    *out = m;
+    return ST_OK;
+}
+
+st_status st_sync(st_model* m) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_sync: NULL model");
+    ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    int32_t h = 0;
+    ST_CUDA_TRY(cudaMemcpy(&h, m->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (h != 0) {
+        ST_CUDA_TRY(cudaMemset(m->d_err, 0, sizeof(int32_t)));
+        return st_fail(h, "device reported %s", st_status_string(h));
+    }
+    return ST_OK;
+}
+
+st_status st_model_set_basis(st_model* m, int32_t ns, int32_t nt, int32_t Nt, const double* phi_s,
+                             const double* T) {
+    if (!m || !phi_s || !T) return st_fail(ST_ERR_ARG, "st_model_set_basis: NULL argument");
+    if (ns < 1 || nt < 1 || Nt < 1 || ns > m->N || nt > Nt)
+        return st_fail(ST_ERR_ARG, "st_model_set_basis: bad sizes");
+    free_reduced(m);
+    free_basis(m);
+    ST_CUDA_TRY(cudaMalloc(&m->d_phi, sizeof(double) * m->N * ns));
+    ST_CUDA_TRY(cudaMalloc(&m->d_T, sizeof(double) * (size_t)Nt * ns * nt));
+    ST_CUDA_TRY(cudaMemcpyAsync(m->d_phi, phi_s, sizeof(double) * m->N * ns,
+                                cudaMemcpyDeviceToDevice, m->stream));
+    ST_CUDA_TRY(cudaMemcpyAsync(m->d_T, T, sizeof(double) * (size_t)Nt * ns * nt,
+                                cudaMemcpyDeviceToDevice, m->stream));
+    m->ns = ns;
+    m->nt = nt;
+    m->Nt = Nt;
+    return ST_OK;
+}
+
+st_status st_model_get_basis(st_model* m, double* phi_s, double* T, int32_t* dims) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_model_get_basis: NULL model");
+    if (!m->d_phi) return st_fail(ST_ERR_STATE, "st_model_get_basis: no basis");
+    if (dims) {
+        dims[0] = m->ns;
+        dims[1] = m->nt;
+        dims[2] = m->Nt;
+    }
+    if (phi_s)
+        ST_CUDA_TRY(cudaMemcpyAsync(phi_s, m->d_phi, sizeof(double) * m->N * m->ns,
+                                    cudaMemcpyDeviceToDevice, m->stream));
+    if (T)
+        ST_CUDA_TRY(cudaMemcpyAsync(T, m->d_T, sizeof(double) * (size_t)m->Nt * m->ns * m->nt,
+                                    cudaMemcpyDeviceToDevice, m->stream));
+    return ST_OK;
+}
+
+st_status st_pod_get_state(st_model* m, double* W, double* V, double* sigma, int32_t* r) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_pod_get_state: NULL model");
+    if (r) *r = m->pod_r;
+    if (m->pod_r == 0) return ST_OK;
+    if (W)
+        ST_CUDA_TRY(cudaMemcpyAsync(W, m->W.p, sizeof(double) * m->N * m->pod_r,
+                                    cudaMemcpyDeviceToDevice, m->stream));
+    if (V)
+        ST_CUDA_TRY(cudaMemcpyAsync(V, m->V.p, sizeof(double) * m->pod_rows * m->pod_r,
+                                    cudaMemcpyDeviceToDevice, m->stream));
+    if (sigma) std::memcpy(sigma, m->sigma.data(), sizeof(double) * m->pod_r);
+    ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return ST_OK;
+}
+
+st_status st_model_get_reduced(st_model* m, double* Ahat, double* G, double* M, double* S,
+                               double* rhs) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_model_get_reduced: NULL model");
+    if (!m->assembled) return st_fail(ST_ERR_STATE, "st_model_get_reduced: not assembled");
+    const size_t ns = m->ns, nt = m->nt, n = ns * nt;
+    ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (Ahat) ST_CUDA_TRY(cudaMemcpy(Ahat, m->d_Ahat, sizeof(double) * m->Q * ns * ns, cudaMemcpyDeviceToHost));
+    if (G) ST_CUDA_TRY(cudaMemcpy(G, m->d_G, sizeof(double) * n * n, cudaMemcpyDeviceToHost));
+    if (M) ST_CUDA_TRY(cudaMemcpy(M, m->d_M, sizeof(double) * ns * nt * nt, cudaMemcpyDeviceToHost));
+    if (S) ST_CUDA_TRY(cudaMemcpy(S, m->d_S, sizeof(double) * ns * nt * nt, cudaMemcpyDeviceToHost));
+    if (rhs) ST_CUDA_TRY(cudaMemcpy(rhs, m->d_rhs, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return ST_OK;
+}
+
+}  // extern "C"
+
+// Used by st_rom_build_basis to replace the basis it produced.
+void st_internal_free_basis(st_model* m) {
+    free_reduced(m);
+    free_basis(m);
+}
+void st_internal_free_reduced(st_model* m) { free_reduced(m); }

@@ -1,0 +1,488 @@
+// Batched online phase (Eq. st-galerkin): for every parameter sample p,
+//   Ahat(mu_p) = sum_q theta_q Ahat_q                       (ns_p x ns_p)
+//   Ahat^st[(i',j'),(i,j)] = delta_{i'i} (M_i - S_i)[j',j]
+//                            - Ahat(mu_p)[i',i] G[(i',j'),(i,j)]   (Eq. ij-block-matrix)
+//   solve Ahat^st uhat = fhat^st + uhat0^st.
+// Samples have individual nested sizes (ns_p, nt_p): the sub-basis
+// i < ns_p, j < nt_p, re-indexed i + ns_p j.
+//
+// One persistent kernel, one CTA per SM, pulls samples from a queue ordered
+// largest first (so the big factorisations start early and the small ones
+// fill the tail).  Each CTA assembles its sample's matrix into a private
+// workspace, factorises it with a right-looking blocked LU with partial
+// pivoting in FP64 (the panel lives in shared memory; the trailing update is
+// a register-tiled 64x64 FP64 product), solves, refines with an FP64
+// residual regenerated from (Ahat, G, M, S) and reports ||r|| / ||rhs||.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int NWARP = NT / 32;
+constexpr int CW = 64;  // trailing-update column chunk
+
+struct SolveArgs {
+    int n_mu, Q, ns, nt, nfull;
+    const double* Ahat;
+    const double* G;
+    const float* G32;
+    const double* M;
+    const double* S;
+    const double* rhs;
+    const double* theta;
+    const int32_t* ns_nt;
+    const int* order;
+    unsigned int* queue;
+    double* uhat;
+    double* rel_res;
+    int32_t* status;
+    double* ws;
+    int refine;
+    int fp32_asm;
+    int nb;
+    int32_t* err;
+};
+
+struct Smem {
+    double* P;    // panel: nfull x nb (ld nfull)
+    double* U;    // nb x CW
+    double* Ah;   // ns_p x ns_p
+    double* b;    // rhs
+    double* x;    // solution
+    double* r;    // residual / correction
+    int* piv;     // pivots
+};
+
+__device__ __forceinline__ void block_argmax(double v, int idx, double* s_val, int* s_idx,
+                                             double& out_v, int& out_i) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (v2 > v || (v2 == v && i2 < idx)) {
+            v = v2;
+            idx = i2;
+        }
+    }
+    if (lane == 0) {
+        s_val[warp] = v;
+        s_idx[warp] = idx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bv = s_val[0];
+        int bi = s_idx[0];
+        for (int w = 1; w < NWARP; ++w)
+            if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bi)) {
+                bv = s_val[w];
+                bi = s_idx[w];
+            }
+        s_val[0] = bv;
+        s_idx[0] = bi;
+    }
+    __syncthreads();
+    out_v = s_val[0];
+    out_i = s_idx[0];
+}
+
+__device__ __forceinline__ double block_sum(double v, double* s_val) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) s_val[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < NWARP; ++w) t += s_val[w];
+    __syncthreads();
+    return t;
+}
+
+// In-place LU with partial pivoting of A (n x n, ld n).  Returns false if a
+// zero pivot occurred (the factorisation still completes, as in LAPACK).
+__device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s_val, int* s_idx) {
+    bool ok = true;
+    const int tid = threadIdx.x;
+    for (int kb = 0; kb < n; kb += nb) {
+        const int w = min(nb, n - kb), rp = n - kb;
+        for (int t = tid; t < rp * w; t += NT) {
+            const int r = t % rp, c = t / rp;
+            s.P[r + c * ld_p] = A[(kb + r) + (int64_t)(kb + c) * n];
+        }
+        __syncthreads();
+        for (int c = 0; c < w; ++c) {
+            double bv = -1.0;
+            int bi = c;
+            for (int r = c + tid; r < rp; r += NT) {
+                const double v = fabs(s.P[r + c * ld_p]);
+                if (v > bv) {
+                    bv = v;
+                    bi = r;
+                }
+            }
+            double mv;
+            int pr;
+            block_argmax(bv, bi, s_val, s_idx, mv, pr);
+            if (tid == 0) s.piv[kb + c] = kb + pr;
+            if (pr != c)
+                for (int cc = tid; cc < w; cc += NT) {
+                    const double t0 = s.P[c + cc * ld_p];
+                    s.P[c + cc * ld_p] = s.P[pr + cc * ld_p];
+                    s.P[pr + cc * ld_p] = t0;
+                }
+            __syncthreads();
+            const double pv = s.P[c + c * ld_p];
+            if (pv == 0.0) {
+                ok = false;
+            } else {
+                const double inv = 1.0 / pv;
+                for (int r = c + 1 + tid; r < rp; r += NT) s.P[r + c * ld_p] *= inv;
+            }
+            __syncthreads();
+            const int nr = rp - c - 1, nc = w - c - 1;
+            if (nr > 0 && nc > 0)
+                for (int t = tid; t < nr * nc; t += NT) {
+                    const int r = c + 1 + t % nr, cc = c + 1 + t / nr;
+                    s.P[r + cc * ld_p] = fma(-s.P[r + c * ld_p], s.P[c + cc * ld_p], s.P[r + cc * ld_p]);
+                }
+            __syncthreads();
+        }
+        for (int t = tid; t < rp * w; t += NT) {
+            const int r = t % rp, c = t / rp;
+            A[(kb + r) + (int64_t)(kb + c) * n] = s.P[r + c * ld_p];
+        }
+        // row interchanges on the columns outside the panel, in pivot order
+        for (int j = tid; j < n - w; j += NT) {
+            const int jj = j < kb ? j : j + w;
+            double* colp = A + (int64_t)jj * n;
+            for (int c = 0; c < w; ++c) {
+                const int pr = s.piv[kb + c];
+                if (pr != kb + c) {
+                    const double t0 = colp[kb + c];
+                    colp[kb + c] = colp[pr];
+                    colp[pr] = t0;
+                }
+            }
+        }
+        __syncthreads();
+        // U12 = L11^{-1} A12 and A22 -= L21 U12, one column chunk at a time
+        const int r22 = n - kb - w;
+        for (int j0 = kb + w; j0 < n; j0 += CW) {
+            const int wc = min(CW, n - j0);
+            for (int t = tid; t < w * wc; t += NT) {
+                const int r = t % w, c = t / w;
+                s.U[r + c * nb] = A[(kb + r) + (int64_t)(j0 + c) * n];
+            }
+            __syncthreads();
+            if (tid < wc) {
+                double* u = s.U + tid * nb;
+                for (int r = 1; r < w; ++r) {
+                    double acc = u[r];
+                    for (int cc = 0; cc < r; ++cc) acc = fma(-s.P[r + cc * ld_p], u[cc], acc);
+                    u[r] = acc;
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < w * wc; t += NT) {
+                const int r = t % w, c = t / w;
+                A[(kb + r) + (int64_t)(j0 + c) * n] = s.U[r + c * nb];
+            }
+            const int tx = tid & 15, ty = tid >> 4;
+            for (int rt = 0; rt < r22; rt += 64) {
+                double acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int bq = 0; bq < 4; ++bq) acc[a][bq] = 0.0;
+                for (int cc = 0; cc < w; ++cc) {
+                    double lv[4], uv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int rr = rt + tx + 16 * a;
+                        lv[a] = rr < r22 ? s.P[(w + rr) + cc * ld_p] : 0.0;
+                    }
+#pragma unroll
+                    for (int bq = 0; bq < 4; ++bq) {
+                        const int c2 = ty + 16 * bq;
+                        uv[bq] = c2 < wc ? s.U[cc + c2 * nb] : 0.0;
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int bq = 0; bq < 4; ++bq) acc[a][bq] = fma(lv[a], uv[bq], acc[a][bq]);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int rr = rt + tx + 16 * a;
+                    if (rr >= r22) continue;
+#pragma unroll
+                    for (int bq = 0; bq < 4; ++bq) {
+                        const int c2 = ty + 16 * bq;
+                        if (c2 >= wc) continue;
+                        double* p = A + (kb + w + rr) + (int64_t)(j0 + c2) * n;
+                        *p -= acc[a][bq];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    return ok;
+}
+
+// x <- A^{-1} x using the LU factors and pivots in A / s.piv.
+__device__ void lu_solve(const double* A, int n, Smem& s, double* x) {
+    const int tid = threadIdx.x;
+    if (tid == 0)
+        for (int i = 0; i < n; ++i) {
+            const int pr = s.piv[i];
+            if (pr != i) {
+                const double t = x[i];
+                x[i] = x[pr];
+                x[pr] = t;
+            }
+        }
+    __syncthreads();
+    for (int c = 0; c < n; ++c) {
+        const double xc = x[c];
+        for (int r = c + 1 + tid; r < n; r += NT) x[r] = fma(-A[r + (int64_t)c * n], xc, x[r]);
+        __syncthreads();
+    }
+    for (int c = n - 1; c >= 0; --c) {
+        if (tid == 0) x[c] /= A[c + (int64_t)c * n];
+        __syncthreads();
+        const double xc = x[c];
+        for (int r = tid; r < c; r += NT) x[r] = fma(-A[r + (int64_t)c * n], xc, x[r]);
+        __syncthreads();
+    }
+}
+
+// Entry (row, col) of the sample's Ahat^st in FP64 (row = i' + a j', col = i + a j).
+__device__ __forceinline__ double st_entry(const SolveArgs& g, const double* Ah, int a, int row,
+                                           int col) {
+    const int ip = row % a, jp = row / a, i = col % a, j = col / a;
+    const int64_t gi = (int64_t)(ip + g.ns * jp) + (int64_t)(i + g.ns * j) * g.nfull;
+    double v = -Ah[ip + i * a] * g.G[gi];
+    if (ip == i) {
+        const int64_t mi = (int64_t)i * g.nt * g.nt + jp + (int64_t)j * g.nt;
+        v += g.M[mi] - g.S[mi];
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
+    extern __shared__ double smem[];
+    __shared__ double s_val[NWARP];
+    __shared__ int s_idx[NWARP];
+    __shared__ int s_item;
+    const int nfull = g.nfull, nb = g.nb;
+    Smem s;
+    s.P = smem;
+    s.U = s.P + (size_t)nfull * nb;
+    s.Ah = s.U + (size_t)nb * CW;
+    s.b = s.Ah + (size_t)g.ns * g.ns;
+    s.x = s.b + nfull;
+    s.r = s.x + nfull;
+    s.piv = reinterpret_cast<int*>(s.r + nfull);
+    double* A = g.ws + (size_t)blockIdx.x * nfull * nfull;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            const unsigned int it = atomicAdd(g.queue, 1u);
+            s_item = it < (unsigned)g.n_mu ? g.order[it] : -1;
+        }
+        __syncthreads();
+        const int p = s_item;
+        __syncthreads();
+        if (p < 0) break;
+        int a = g.ns, bt = g.nt;
+        if (g.ns_nt) {
+            a = g.ns_nt[2 * p];
+            bt = g.ns_nt[2 * p + 1];
+        }
+        double* up = g.uhat + (size_t)p * nfull;
+        if (a < 1 || a > g.ns || bt < 1 || bt > g.nt) {
+            if (tid == 0) {
+                if (g.status) g.status[p] = ST_ERR_ARG;
+                if (g.rel_res) g.rel_res[p] = __longlong_as_double(0x7ff8000000000000LL);
+                st_dev_error(g.err, ST_ERR_ARG);
+            }
+            continue;
+        }
+        const int n = a * bt;
+        // Ahat(mu_p) restricted to the leading a modes
+        for (int t = tid; t < a * a; t += NT) {
+            const int ip = t % a, i = t / a;
+            double v = 0.0;
+            for (int q = 0; q < g.Q; ++q)
+                v = fma(g.theta[(int64_t)p * g.Q + q], g.Ahat[(int64_t)q * g.ns * g.ns + ip + (int64_t)i * g.ns], v);
+            s.Ah[t] = v;
+        }
+        for (int t = tid; t < n; t += NT) {
+            const int i = t % a, j = t / a;
+            s.b[t] = g.rhs[i + g.ns * j];
+        }
+        __syncthreads();
+        // assemble Ahat^st (FP64, or FP32 products in the FP32-assembly mode)
+        for (int64_t t = tid; t < (int64_t)n * n; t += NT) {
+            const int row = (int)(t % n), col = (int)(t / n);
+            double v;
+            if (g.fp32_asm) {
+                const int ip = row % a, jp = row / a, i = col % a, j = col / a;
+                const int64_t gi = (int64_t)(ip + g.ns * jp) + (int64_t)(i + g.ns * j) * nfull;
+                float f = -(float)s.Ah[ip + i * a] * g.G32[gi];
+                if (ip == i) {
+                    const int64_t mi = (int64_t)i * g.nt * g.nt + jp + (int64_t)j * g.nt;
+                    f += (float)(g.M[mi] - g.S[mi]);
+                }
+                v = (double)f;
+            } else {
+                v = st_entry(g, s.Ah, a, row, col);
+            }
+            A[row + (int64_t)col * n] = v;
+        }
+        __syncthreads();
+        const bool ok = lu_factor(A, n, nfull, nb, s, s_val, s_idx);
+        if (!ok) {
+            for (int t = tid; t < n; t += NT) up[t] = 0.0;
+            if (tid == 0) {
+                if (g.status) g.status[p] = ST_ERR_SINGULAR;
+                if (g.rel_res) g.rel_res[p] = __longlong_as_double(0x7ff0000000000000LL);
+                st_dev_error(g.err, ST_ERR_SINGULAR);
+            }
+            __syncthreads();
+            continue;
+        }
+        for (int t = tid; t < n; t += NT) s.x[t] = s.b[t];
+        __syncthreads();
+        lu_solve(A, n, s, s.x);
+        double rn = 0.0;
+        for (int step = 0; step <= g.refine; ++step) {
+            // r = b - Ahat^st x (FP64, matrix regenerated from the reduced operators)
+            for (int row = tid; row < n; row += NT) {
+                double acc = s.b[row];
+                for (int col = 0; col < n; ++col) acc = fma(-st_entry(g, s.Ah, a, row, col), s.x[col], acc);
+                s.r[row] = acc;
+            }
+            __syncthreads();
+            double loc = 0.0;
+            for (int t = tid; t < n; t += NT) loc = fma(s.r[t], s.r[t], loc);
+            rn = block_sum(loc, s_val);
+            if (step == g.refine) break;
+            lu_solve(A, n, s, s.r);
+            for (int t = tid; t < n; t += NT) s.x[t] += s.r[t];
+            __syncthreads();
+        }
+        double loc = 0.0;
+        for (int t = tid; t < n; t += NT) loc = fma(s.b[t], s.b[t], loc);
+        const double bn = block_sum(loc, s_val);
+        for (int t = tid; t < n; t += NT) up[t] = s.x[t];
+        if (tid == 0) {
+            const double rel = bn > 0.0 ? sqrt(rn) / sqrt(bn) : sqrt(rn);
+            const bool fin = isfinite(rel);
+            if (g.rel_res) g.rel_res[p] = rel;
+            if (g.status) g.status[p] = fin ? ST_OK : ST_ERR_NONFINITE;
+            if (!fin) st_dev_error(g.err, ST_ERR_NONFINITE);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- largest-first queue order ---------------------------------------------
+__global__ void size_hist_kernel(int n_mu, int ns, int nt, const int32_t* __restrict__ ns_nt,
+                                 int* npv, int* hist) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_mu; p += gridDim.x * blockDim.x) {
+        int a = ns, b = nt;
+        if (ns_nt) {
+            a = ns_nt[2 * p];
+            b = ns_nt[2 * p + 1];
+        }
+        int n = (a >= 1 && a <= ns && b >= 1 && b <= nt) ? a * b : 0;
+        npv[p] = n;
+        atomicAdd(hist + n, 1);
+    }
+}
+
+__global__ void size_scan_kernel(int nfull, int* hist) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int run = 0;
+        for (int s = nfull; s >= 0; --s) {
+            const int c = hist[s];
+            hist[s] = run;
+            run += c;
+        }
+    }
+}
+
+__global__ void size_scatter_kernel(int n_mu, const int* __restrict__ npv, int* hist, int* order) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_mu; p += gridDim.x * blockDim.x)
+        order[atomicAdd(hist + npv[p], 1)] = p;
+}
+
+}  // namespace
+
+extern "C" st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta,
+                                  const int32_t* ns_nt, double* uhat, double* rel_res,
+                                  int32_t* status) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_rom_solve: NULL model");
+    if (!m->assembled) return st_fail(ST_ERR_STATE, "st_rom_solve: reduced operators not assembled");
+    if (n_mu < 0 || (n_mu > 0 && (!theta || !uhat))) return st_fail(ST_ERR_ARG, "st_rom_solve: bad arguments");
+    if (n_mu == 0) return ST_OK;
+    const int ns = m->ns, nt = m->nt, nfull = ns * nt;
+    cudaStream_t st = m->stream;
+    // shared-memory plan: the panel width shrinks if a wide model does not fit
+    int nb = 32;
+    auto smem_for = [&](int b) {
+        return sizeof(double) * ((size_t)nfull * b + (size_t)b * CW + (size_t)ns * ns + 3 * (size_t)nfull) +
+               sizeof(int) * (size_t)nfull + 64;
+    };
+    int max_optin = 0;
+    ST_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+    while (nb > 4 && smem_for(nb) > (size_t)max_optin) nb /= 2;
+    const size_t smem = smem_for(nb);
+    if (smem > (size_t)max_optin) return st_fail(ST_ERR_ARG, "st_rom_solve: ns*nt = %d too large", nfull);
+    ST_CUDA_TRY(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, NT, smem));
+    const int blocks = std::max(1, std::min(per_sm, 2)) * m->num_sms;
+    const size_t ints = (size_t)2 * n_mu + nfull + 1 + 16;
+    ST_TRY(st_grow(m, m->ws_solve, sizeof(double) * (size_t)blocks * nfull * nfull + sizeof(int) * ints));
+    double* ws = (double*)m->ws_solve.p;
+    int* npv = (int*)(ws + (size_t)blocks * nfull * nfull);
+    int* order = npv + n_mu;
+    int* hist = order + n_mu;
+    ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n_mu + 255) / 256, 4 * m->num_sms));
+    size_hist_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, ns_nt, npv, hist);
+    size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
+    size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
+    ST_TRY(st_check_launch("solve order"));
+    ST_CUDA_TRY(cudaMemsetAsync(m->d_bar + 3, 0, sizeof(unsigned int), st));
+    SolveArgs g;
+    g.n_mu = n_mu;
+    g.Q = m->Q;
+    g.ns = ns;
+    g.nt = nt;
+    g.nfull = nfull;
+    g.Ahat = m->d_Ahat;
+    g.G = m->d_G;
+    g.G32 = m->d_G32;
+    g.M = m->d_M;
+    g.S = m->d_S;
+    g.rhs = m->d_rhs;
+    g.theta = theta;
+    g.ns_nt = ns_nt;
+    g.order = order;
+    g.queue = m->d_bar + 3;
+    g.uhat = uhat;
+    g.rel_res = rel_res;
+    g.status = status;
+    g.ws = ws;
+    g.refine = m->opt.refine_steps;
+    g.fp32_asm = m->opt.precision == ST_FP32_ASSEMBLY;
+    g.nb = nb;
+    g.err = m->d_err;
+    solve_kernel<<<blocks, NT, smem, st>>>(g);
+    return st_check_launch("solve");
+}
