@@ -34,28 +34,45 @@ constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
 
 // ---------------------------------------------------------------------------
-// tau = eps * max_j ||U[:, j]||
-__global__ void colnorm_max_kernel(int64_t N, int m, const double* __restrict__ U, double eps,
-                                   double* tau) {
+// tau = eps * max_j ||U[:, j]||: block (j, c) sums column j over row chunk c
+// into part[j * chunks + c]; one block then finishes the norms and the max.
+__global__ void colnorm_part_kernel(int64_t N, const double* __restrict__ U, int chunks,
+                                    double* part) {
     __shared__ double s_part[NWARP];
-    double mx = 0.0;
-    for (int j = 0; j < m; ++j) {
-        double acc = 0.0;
-        for (int64_t i = threadIdx.x; i < N; i += NT) {
-            const double v = U[i + (int64_t)j * N];
-            acc = fma(v, v, acc);
-        }
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < NWARP; ++w) s += s_part[w];
-            mx = fmax(mx, sqrt(s));
-        }
-        __syncthreads();
+    const int j = blockIdx.x, c = blockIdx.y;
+    const int64_t len = (N + chunks - 1) / chunks;
+    const int64_t r0 = (int64_t)c * len, r1 = min(N, r0 + len);
+    double acc = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += NT) {
+        const double v = U[i + (int64_t)j * N];
+        acc = fma(v, v, acc);
     }
-    if (threadIdx.x == 0) *tau = eps * mx;
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < NWARP; ++w) s += s_part[w];
+        part[(int64_t)j * chunks + c] = s;
+    }
+}
+
+__global__ void colnorm_max_kernel(int m, int chunks, const double* __restrict__ part, double eps,
+                                   double* tau) {
+    __shared__ double s_max[NT];
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < m; j += NT) {
+        double s = 0.0;
+        for (int c = 0; c < chunks; ++c) s += part[(int64_t)j * chunks + c];
+        mx = fmax(mx, sqrt(s));
+    }
+    s_max[threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int t = 0; t < NT; ++t) v = fmax(v, s_max[t]);
+        *tau = eps * v;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -165,6 +182,51 @@ __global__ void __launch_bounds__(NT) gs2_kernel(Gs2Args a) {
 }
 
 // ---------------------------------------------------------------------------
+// Cholesky QR step for a well-conditioned block (the second block pass):
+// G = R^T R (upper R, written with leading dimension ldr) and Rinv = R^{-1}
+// (ld k).  A pivot below 1e-8 of its diagonal entry of G sets *fail so the
+// host can fall back to column-wise Gram-Schmidt.
+__global__ void __launch_bounds__(NT) chol_inv_kernel(int k, const double* __restrict__ G, double* R,
+                                                      int ldr, double* Rinv, int* fail) {
+    __shared__ double s_d;
+    for (int t = threadIdx.x; t < k * k; t += NT) {
+        const int i = t % k, j = t / k;
+        R[i + (int64_t)j * ldr] = 0.0;
+        Rinv[t] = 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        if (threadIdx.x == 0) {
+            double d = G[j + (int64_t)j * k];
+            for (int i = 0; i < j; ++i) d -= R[i + (int64_t)j * ldr] * R[i + (int64_t)j * ldr];
+            if (!(d > 1e-16 * G[j + (int64_t)j * k])) {
+                *fail = 1;
+                d = 1.0;
+            }
+            s_d = sqrt(d);
+            R[j + (int64_t)j * ldr] = s_d;
+        }
+        __syncthreads();
+        const double rjj = s_d;
+        for (int c = j + 1 + threadIdx.x; c < k; c += NT) {
+            double v = G[j + (int64_t)c * k];
+            for (int i = 0; i < j; ++i) v -= R[i + (int64_t)j * ldr] * R[i + (int64_t)c * ldr];
+            R[j + (int64_t)c * ldr] = v / rjj;
+        }
+        __syncthreads();
+    }
+    // Rinv column c solves R x = e_c (upper triangular back substitution)
+    for (int c = threadIdx.x; c < k; c += NT) {
+        double* x = Rinv + (int64_t)c * k;
+        for (int i = c; i >= 0; --i) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int l = i + 1; l <= c; ++l) v -= R[i + (int64_t)l * ldr] * x[l];
+            x[i] = v / R[i + (int64_t)i * ldr];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // X = Q^T for Q = [[diag(sigma), L], [0, P(0:k, :)]]:  X is (r + m) x (r + k).
 __global__ void build_qt_kernel(int r, int k, int m, const double* __restrict__ sigma,
                                 const double* __restrict__ L, int ldl, const double* __restrict__ P,
@@ -193,7 +255,10 @@ __global__ void eye_kernel(int n, double* Y, int ldy) {
 // ---------------------------------------------------------------------------
 // One-sided Jacobi on the columns of X (m x n), rotations accumulated into Y
 // (n x n).  Round-robin ordering: every round pairs each column once, a
-// sweep of n_p - 1 rounds meets every pair; one warp per pair.
+// sweep of n_p - 1 rounds meets every pair.  One warp per pair and one warp
+// per block, so the pairs of a round spread over all SMs (the rotations are
+// FP64-throughput bound).  Squared column norms are kept in nrm2 and updated
+// with each rotation; they are recomputed at the start of every sweep.
 struct JacArgs {
     int m, n;
     double* X;
@@ -202,8 +267,11 @@ struct JacArgs {
     int ldy;
     int max_sweeps;
     double tol;
-    int* flags;   // [3]
-    int* sweeps;  // out
+    int* flags;    // [3]
+    int* sweeps;   // out
+    double* nrm2;  // [n + 1]: squared column norms, then the largest
+    double cut;    // relative singular-value cut below which columns are dropped
+    int* perm;     // [n] visiting order of the current sweep
     GridBarrier bar;
 };
 
@@ -217,50 +285,104 @@ __device__ __forceinline__ void jacobi_pair_rot(double alpha, double beta, doubl
     s = c * t;
 }
 
-__global__ void __launch_bounds__(NT) jacobi_kernel(JacArgs a) {
-    __shared__ int s_flag;
+constexpr int JW = 4;  // warps per Jacobi pair (one pair per block)
+
+__device__ __forceinline__ double jac_block_sum(double v, double* s_red) {
+    v = warp_sum(v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = blockIdx.x * NWARP + warp, nw = gridDim.x * NWARP;
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < JW; ++w) t += s_red[w];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
+    __shared__ int s_flag;
+    __shared__ double s_red[JW];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int gw = blockIdx.x, nw = gridDim.x;
     const int np = a.n + (a.n & 1);
     const int npairs = np / 2;
     int sweep = 0;
     bool converged = false;
     for (; sweep < a.max_sweeps; ++sweep) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[(sweep + 1) % 3] = 0;
+        if (blockIdx.x == 0 && tid == 0) {
+            a.flags[(sweep + 1) % 3] = 0;
+            if (sweep == 0) a.nrm2[a.n] = 0.0;
+        }
+        for (int c = gw; c < a.n; c += nw) {
+            const double* xc = a.X + (int64_t)c * a.ldx;
+            double acc = 0.0;
+            for (int r = tid; r < a.m; r += nthr) {
+                const double u = __ldcg(xc + r);
+                acc = fma(u, u, acc);
+            }
+            acc = jac_block_sum(acc, s_red);
+            if (tid == 0) {
+                __stcg(a.nrm2 + c, acc);
+                // largest squared norm (positive doubles order like their bit patterns)
+                if (sweep == 0)
+                    atomicMax(reinterpret_cast<unsigned long long*>(a.nrm2 + a.n),
+                              (unsigned long long)__double_as_longlong(acc));
+            }
+        }
+        if (!grid_sync(a.bar, &s_flag)) return;
+        // visit columns in decreasing-norm order this sweep (the tournament
+        // pairs positions; perm maps positions to columns)
+        if (blockIdx.x == 0) {
+            for (int c = tid; c < a.n; c += nthr) {
+                const double v = __ldcg(a.nrm2 + c);
+                int rank = 0;
+                for (int d = 0; d < a.n; ++d) {
+                    const double w = __ldcg(a.nrm2 + d);
+                    rank += (w > v) || (w == v && d < c);
+                }
+                __stcg(a.perm + rank, c);
+            }
+        }
+        if (!grid_sync(a.bar, &s_flag)) return;
+        // pairs of columns that both lie below the truncation cut are dropped
+        // after the SVD whatever their rotation, so they are not rotated
+        const double cut2 = a.cut * a.cut * __ldcg(a.nrm2 + a.n);
         for (int t = 0; t < np - 1; ++t) {
             for (int q = gw; q < npairs; q += nw) {
                 int i, j;
                 if (q == 0) { i = t; j = np - 1; }
                 else { i = (t + q) % (np - 1); j = (t - q + np - 1) % (np - 1); }
                 if (i >= a.n || j >= a.n) continue;
+                i = __ldcg(a.perm + i);
+                j = __ldcg(a.perm + j);
                 double* xi = a.X + (int64_t)i * a.ldx;
                 double* xj = a.X + (int64_t)j * a.ldx;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int r = lane; r < a.m; r += 32) {
-                    const double u = __ldcg(xi + r), v = __ldcg(xj + r);
-                    al = fma(u, u, al);
-                    be = fma(v, v, be);
-                    ga = fma(u, v, ga);
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga != 0.0 && fabs(ga) > a.tol * sqrt(al) * sqrt(be)) {
+                const double al = __ldcg(a.nrm2 + i), be = __ldcg(a.nrm2 + j);
+                double ga = 0.0;
+                for (int r = tid; r < a.m; r += nthr) ga = fma(__ldcg(xi + r), __ldcg(xj + r), ga);
+                ga = jac_block_sum(ga, s_red);
+                if ((al > cut2 || be > cut2) && fabs(ga) > a.tol * sqrt(al) * sqrt(be)) {
                     double c, s;
                     jacobi_pair_rot(al, be, ga, c, s);
-                    for (int r = lane; r < a.m; r += 32) {
+                    for (int r = tid; r < a.m; r += nthr) {
                         const double u = __ldcg(xi + r), v = __ldcg(xj + r);
                         __stcg(xi + r, c * u - s * v);
                         __stcg(xj + r, s * u + c * v);
                     }
                     double* yi = a.Y + (int64_t)i * a.ldy;
                     double* yj = a.Y + (int64_t)j * a.ldy;
-                    for (int r = lane; r < a.n; r += 32) {
+                    for (int r = tid; r < a.n; r += nthr) {
                         const double u = __ldcg(yi + r), v = __ldcg(yj + r);
                         __stcg(yi + r, c * u - s * v);
                         __stcg(yj + r, s * u + c * v);
                     }
-                    if (lane == 0) atomicExch(a.flags + sweep % 3, 1);
+                    if (tid == 0) {
+                        // new squared norms: c^2 al - 2cs ga + s^2 be and s^2 al + 2cs ga + c^2 be
+                        const double cs2 = 2.0 * c * s * ga;
+                        __stcg(a.nrm2 + i, fmax(c * c * al - cs2 + s * s * be, 0.0));
+                        __stcg(a.nrm2 + j, fmax(s * s * al + cs2 + c * c * be, 0.0));
+                        atomicExch(a.flags + sweep % 3, 1);
+                    }
                 }
             }
             if (!grid_sync(a.bar, &s_flag)) return;
@@ -271,7 +393,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(JacArgs a) {
             break;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
         *a.sweeps = sweep;
         if (!converged) st_dev_error(a.bar.err, ST_ERR_NOT_CONVERGED);
     }
@@ -468,9 +590,9 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         gs_blocks = std::max(1, std::min(per_sm, 1)) * m->num_sms;
         gs_blocks = (int)std::min<int64_t>(gs_blocks, std::max<int64_t>(1, N / 64));
     }
-    const size_t szPart = (size_t)std::max(gs_blocks, 1) * pdim;
+    const size_t szPart = std::max((size_t)std::max(gs_blocks, 1) * pdim, (size_t)64 * Nt);
     const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 2 * szX + (size_t)cap * rmax * 2 +
-                           szPart + pdim + 4 * cap + 16;
+                           szPart + pdim + 4 * cap + 32;
     ST_TRY(st_grow(m, m->ws_pod, sizeof(double) * doubles + sizeof(int) * (2 * cap + 16)));
     double* W2 = (double*)m->ws_pod.p;
     double* V2 = W2 + szW2;
@@ -489,7 +611,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     double* d_sig = hbuf + pdim;         // [cap] current sigma (device copy)
     double* d_sig_sorted = d_sig + cap;  // [cap]
     double* d_sig_tmp = d_sig_sorted + cap;
-    double* d_scalar = d_sig_tmp + cap;  // [16]: tau, dot
+    double* d_scalar = d_sig_tmp + cap + 8;  // [16]: tau, dot (d_sig_tmp[cap] is the Jacobi norm max)
     int* d_int = (int*)(d_scalar + 16);  // [16]: k, r_new, sweeps, flags[3]
     int* d_perm = d_int + 16;            // [cap]
     double* W = (double*)m->W.p;
@@ -498,8 +620,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     int jac_blocks_max = 0;
     {
         int per_sm = 0;
-        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, NT, 0));
-        jac_blocks_max = std::max(1, per_sm) * m->num_sms;
+        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 32 * JW, 0));
+        jac_blocks_max = std::max(1, std::min(per_sm, 2)) * m->num_sms;
     }
     const GridBarrier bar{m->d_bar, m->d_bar + 1, m->d_bar + 2, m->d_err, m->opt.spin_limit};
     int r = 0;
@@ -525,8 +647,13 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     };
     for (int p = 0; p < n_mu; ++p) {
         const double* Up = snapshots + (size_t)p * Nt * N;
-        colnorm_max_kernel<<<1, NT, 0, st>>>(N, Nt, Up, m->opt.eps_svd, d_scalar);
-        ST_TRY(st_check_launch("colnorm_max"));
+        {
+            const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(64, N / 2048));
+            colnorm_part_kernel<<<dim3(Nt, chunks), NT, 0, st>>>(N, Up, chunks, partial);
+            ST_TRY(st_check_launch("colnorm_part"));
+            colnorm_max_kernel<<<1, NT, 0, st>>>(Nt, chunks, partial, m->opt.eps_svd, d_scalar);
+            ST_TRY(st_check_launch("colnorm_max"));
+        }
         ST_CUDA_TRY(cudaMemcpyAsync(E, Up, sizeof(double) * szE, cudaMemcpyDeviceToDevice, st));
         double* J = W + (size_t)r * N;
         int k = 0;
@@ -538,12 +665,26 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             int k1 = 0;
             ST_TRY(read_k(&k1));
             if (k1 > 0) {
-                // second block pass: L2 = W^T J1, J1 - W L2 = J P2; L += L2 P1, P = P2 P1
+                // second block pass: L2 = W^T J1, E2 = J1 - W L2 = J P2 by Cholesky QR
+                // (E2 is orthonormal up to the rounding carried along W, so its
+                // Gram matrix is well conditioned); L += L2 P1, P = P2 P1
                 ST_TRY(st_dgemm(m, true, false, r, k1, N, 1.0, W, N, J, N, 0.0, L2, rmax));
                 ST_CUDA_TRY(cudaMemcpyAsync(E, J, sizeof(double) * N * k1, cudaMemcpyDeviceToDevice, st));
                 ST_TRY(st_dgemm(m, false, false, N, k1, r, -1.0, W, N, L2, rmax, 1.0, E, N));
-                ST_TRY(run_gs(E, k1, J, P2, nullptr));
-                ST_TRY(read_k(&k));
+                ST_TRY(st_dgemm(m, true, false, k1, k1, N, 1.0, E, N, E, N, 0.0, Y, k1));
+                ST_CUDA_TRY(cudaMemsetAsync(d_int + 6, 0, sizeof(int), st));
+                chol_inv_kernel<<<1, NT, 0, st>>>(k1, Y, P2, k1, X, d_int + 6);
+                ST_TRY(st_check_launch("chol_inv"));
+                int chol_fail = 0;
+                ST_CUDA_TRY(cudaMemcpyAsync(&chol_fail, d_int + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
+                ST_CUDA_TRY(cudaStreamSynchronize(st));
+                if (!chol_fail) {
+                    ST_TRY(st_dgemm(m, false, false, N, k1, k1, 1.0, E, N, X, k1, 0.0, J, N));
+                    k = k1;
+                } else {
+                    ST_TRY(run_gs(E, k1, J, P2, nullptr));
+                    ST_TRY(read_k(&k));
+                }
                 ST_TRY(st_dgemm(m, false, false, r, Nt, k1, 1.0, L2, rmax, P1, Nt, 1.0, L, rmax));
                 if (k > 0) ST_TRY(st_dgemm(m, false, false, k, Nt, k1, 1.0, P2, k1, P1, Nt, 0.0, P, Nt));
             }
@@ -564,11 +705,13 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
         {
             const int npairs = (ncols + 1) / 2;
-            int jb = std::max(1, std::min(jac_blocks_max, (npairs + NWARP - 1) / NWARP));
+            int jb = std::max(1, std::min(jac_blocks_max, npairs));
+            // stop when every pair is orthogonal to m * eps relative
             JacArgs ja{mrows, ncols, X, cap, Y, cap, m->opt.jacobi_sweeps,
-                       std::sqrt((double)mrows) * 2.220446049250313e-16, d_int + 3, d_int + 2, bar};
+                       (double)mrows * 2.220446049250313e-16, d_int + 3, d_int + 2, d_sig_tmp,
+                       0.1 * m->opt.eps_sv, d_perm, bar};
             void* args[] = {&ja};
-            ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(jb), dim3(NT), args, 0, st));
+            ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(jb), dim3(32 * JW), args, 0, st));
         st_count_launch();
         }
         sort_kernel<<<1, 1024, 0, st>>>(mrows, ncols, X, cap, m->opt.eps_sv, rmax, d_sig_sorted,
