@@ -202,6 +202,28 @@ st_status st_model_get_reduced(st_model* m, double* Ahat, double* G, double* M, 
 st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta, const int32_t* ns_nt,
                        double* uhat, double* rel_res, int32_t* status);
 
+/* st_rom_solve without any device allocation.  This entry point has no
+ * counterpart in the paper; it exists for callers that cannot allocate device
+ * memory during a solve -- services running under a fixed, pre-reserved memory
+ * budget (an allocation there may stall or fail), programs whose device memory
+ * belongs to an outside pool that forbids side allocations, and code issuing
+ * the solve where allocation calls are not allowed.
+ * Same arguments, results and status codes as st_rom_solve.  All scratch lives
+ * in one fixed 32 MiB device array inside the library (every GPU that loads
+ * the library holds it until the process exits); the caller still passes the
+ * inputs and outputs, and the call makes no cudaMalloc/cudaFree or other
+ * allocating call.  Limit: 4*(2*n_mu + ns*nt + 17) bytes (rounded up to 256)
+ * plus 8*(ns*nt)^2 bytes must fit in 32 MiB, else ST_ERR_ARG with a message;
+ * when fewer than one block per SM fits, fewer blocks run (slower, same
+ * results).  The first call on a device looks up that array's device address
+ * (once per device, with the model's device current); make that first call
+ * before any stream capture.  Every call uses the same array and zeroes what
+ * must start at zero: calls that overlap on the GPU (other streams, other
+ * models on the same device) race and must be serialised by the caller. */
+st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double* theta,
+                              const int32_t* ns_nt, double* uhat, double* rel_res,
+                              int32_t* status);
+
 /* Reconstruction u^st ~= Phi_st uhat (Eq. ststateapproximation) by blocks:
  *   C[i,k] = sum_j uhat[i + ns_p j] phi_t^{i,j}[k],  u^k = Phi_s C[:,k].
  *   uhat  dev [n_mu x ns*nt] as written by st_rom_solve; ns_nt as there

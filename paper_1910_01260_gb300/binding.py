@@ -71,6 +71,7 @@ _SIGS = {
     "st_rom_assemble": (c_int32, [_P, _P, c_int32, _P, _P, _P]),
     "st_model_get_reduced": (c_int32, [_P, _P, _P, _P, _P, _P]),
     "st_rom_solve": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
+    "st_rom_solve_static": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_reconstruct": (c_int32, [_P, c_int32, _P, _P, _P, c_int32, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -209,6 +210,10 @@ class Model:
     def st_rom_solve(self, n_mu, theta, ns_nt, uhat, rel_res=None, status=None) -> None:
         check(lib.st_rom_solve(self.handle, n_mu, ptr(theta), ptr(ns_nt), ptr(uhat), ptr(rel_res),
                                ptr(status)))
+
+    def st_rom_solve_static(self, n_mu, theta, ns_nt, uhat, rel_res=None, status=None) -> None:
+        check(lib.st_rom_solve_static(self.handle, n_mu, ptr(theta), ptr(ns_nt), ptr(uhat),
+                                      ptr(rel_res), ptr(status)))
 
     def st_rom_reconstruct(self, n_mu, uhat, ns_nt, u=None, n_out=0, Cout=None, y=None) -> None:
         check(lib.st_rom_reconstruct(self.handle, n_mu, ptr(uhat), ptr(ns_nt), ptr(u), n_out,

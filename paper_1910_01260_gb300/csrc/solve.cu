@@ -486,3 +486,133 @@ extern "C" st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta
     solve_kernel<<<blocks, NT, smem, st>>>(g);
     return st_check_launch("solve");
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of st_rom_solve.
+//
+// Some callers must not allocate device memory while they solve: code that
+// runs with a fixed, pre-reserved memory budget (real-time or embedded
+// services where an allocation can stall or fail at the worst moment),
+// callers whose device memory is owned by an outside pool or allocator that
+// forbids side allocations, and callers that issue the solve from a context
+// where allocation calls are not permitted.  For them this entry point keeps
+// all of its scratch (per-block factorisation workspace, queue order, size
+// histogram, queue counter) in one file-scope device array of fixed size;
+// it calls no cudaMalloc/cudaFree and no allocating library routine.  The
+// caller still passes the inputs and outputs.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 32u << 20;  // 32 MiB, held by every GPU that loads the library
+static __device__ __align__(256) unsigned char g_solve_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_solve_scratch on the current device, looked up once
+// per device (the symbol name on the host is only a stand-in).
+st_status scratch_address(int device, void** out) {
+    if (device < 0 || device >= kMaxDevices)
+        return st_fail(ST_ERR_ARG, "st_rom_solve_static: device ordinal %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_solve_scratch);
+        if (e != cudaSuccess || !p)
+            return st_fail(ST_ERR_CUDA, "st_rom_solve_static: cudaGetSymbolAddress failed: %s",
+                           cudaGetErrorString(e));
+        g_scratch_addr[device] = p;
+    }
+    *out = g_scratch_addr[device];
+    return ST_OK;
+}
+
+}  // namespace
+
+extern "C" st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double* theta,
+                                         const int32_t* ns_nt, double* uhat, double* rel_res,
+                                         int32_t* status) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_rom_solve_static: NULL model");
+    if (!m->assembled) return st_fail(ST_ERR_STATE, "st_rom_solve_static: reduced operators not assembled");
+    if (n_mu < 0 || (n_mu > 0 && (!theta || !uhat)))
+        return st_fail(ST_ERR_ARG, "st_rom_solve_static: bad arguments");
+    if (n_mu == 0) return ST_OK;
+    const int ns = m->ns, nt = m->nt, nfull = ns * nt;
+    cudaStream_t st = m->stream;
+    int cur = -1;
+    ST_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != m->device)
+        return st_fail(ST_ERR_STATE, "st_rom_solve_static: current device %d is not the model's device %d",
+                       cur, m->device);
+    void* base = nullptr;
+    ST_TRY(scratch_address(m->device, &base));
+    // scratch layout: [counter | npv (n_mu) | order (n_mu) | hist (nfull + 1)] then
+    // one nfull x nfull FP64 workspace per resident block
+    const size_t int_bytes = ((sizeof(int) * ((size_t)2 * n_mu + nfull + 1 + 16)) + 255) / 256 * 256;
+    const size_t mat_bytes = sizeof(double) * (size_t)nfull * nfull;
+    if (int_bytes + mat_bytes > kStaticScratchBytes)
+        return st_fail(ST_ERR_ARG,
+                       "st_rom_solve_static: n_mu = %d with ns*nt = %d needs %zu bytes of scratch, "
+                       "more than the fixed %zu",
+                       n_mu, nfull, int_bytes + mat_bytes, kStaticScratchBytes);
+    int nb = 32;
+    auto smem_for = [&](int b) {
+        return sizeof(double) * ((size_t)nfull * b + (size_t)b * CW + (size_t)ns * ns + 3 * (size_t)nfull) +
+               sizeof(int) * (size_t)nfull + 64;
+    };
+    int max_optin = 0;
+    ST_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+    while (nb > 4 && smem_for(nb) > (size_t)max_optin) nb /= 2;
+    const size_t smem = smem_for(nb);
+    if (smem > (size_t)max_optin)
+        return st_fail(ST_ERR_ARG, "st_rom_solve_static: ns*nt = %d too large", nfull);
+    ST_CUDA_TRY(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, NT, smem));
+    const size_t fit = (kStaticScratchBytes - int_bytes) / mat_bytes;
+    const int blocks = (int)std::max<size_t>(
+        1, std::min<size_t>(fit, (size_t)std::max(1, std::min(per_sm, 2)) * m->num_sms));
+    unsigned char* sb = static_cast<unsigned char*>(base);
+    unsigned int* queue = reinterpret_cast<unsigned int*>(sb);
+    int* npv = reinterpret_cast<int*>(sb) + 16;
+    int* order = npv + n_mu;
+    int* hist = order + n_mu;
+    double* ws = reinterpret_cast<double*>(sb + int_bytes);
+    // the array keeps the previous call's contents: zero what must start at zero
+    ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
+    ST_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st));
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n_mu + 255) / 256, 4 * m->num_sms));
+    size_hist_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, ns_nt, npv, hist);
+    size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
+    size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
+    ST_TRY(st_check_launch("solve_static order"));
+    SolveArgs g;
+    g.n_mu = n_mu;
+    g.Q = m->Q;
+    g.ns = ns;
+    g.nt = nt;
+    g.nfull = nfull;
+    g.Ahat = m->d_Ahat;
+    g.G = m->d_G;
+    g.G32 = m->d_G32;
+    g.M = m->d_M;
+    g.S = m->d_S;
+    g.rhs = m->d_rhs;
+    g.theta = theta;
+    g.ns_nt = ns_nt;
+    g.order = order;
+    g.queue = queue;
+    g.uhat = uhat;
+    g.rel_res = rel_res;
+    g.status = status;
+    g.ws = ws;
+    g.refine = m->opt.refine_steps;
+    g.fp32_asm = m->opt.precision == ST_FP32_ASSEMBLY;
+    g.nb = nb;
+    g.err = m->d_err;
+    solve_kernel<<<blocks, NT, smem, st>>>(g);
+    return st_check_launch("solve_static");
+}
