@@ -324,6 +324,31 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         e2e_ms = float(t.item())
     e2e_value = world * N_BATCH / (e2e_ms / 1e3)
 
+    # ---- online phase alone, per precision mode (same model and batch) ---
+    online = {}
+    ref_uhat = uhat.clone()
+    for name, prec, refine in (("fp64_lu", st.ST_FP64, 1), ("fp32_lu_fp64_refine3", st.ST_FP32_LU, 3)):
+        m.st_model_set_options(precision=prec, refine_steps=refine)
+        m.st_rom_solve(N_BATCH, th_d, sz_d, uhat, res, s_status)
+        torch.cuda.synchronize()
+        o0 = torch.cuda.Event(enable_timing=True)
+        o1 = torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for _ in range(args.steps):
+            m.st_rom_solve(N_BATCH, th_d, sz_d, uhat, res, s_status)
+            m.st_rom_reconstruct(N_BATCH, uhat, sz_d, None, 1, Cout, y)
+        o1.record(stream)
+        torch.cuda.synchronize()
+        ms = o0.elapsed_time(o1) / args.steps
+        diff = float(((uhat - ref_uhat).abs().max(dim=1).values /
+                      ref_uhat.abs().max(dim=1).values.clamp_min(1e-300)).max())
+        online[name] = {"ms": ms, "solves_per_s": N_BATCH / (ms / 1e3),
+                        "max_rel_res": float(res.max()), "status_ok": int((s_status == 0).sum()),
+                        "max_rel_diff_vs_fp64": diff}
+    m.st_model_set_options(precision=st.ST_FP64, refine_steps=1)
+    uhat.copy_(ref_uhat)
+    m.st_sync()
+
     # ---- accuracy of the ROM against the FOM on sampled batch parameters -
     acc = {}
     sel = []
@@ -375,6 +400,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                            "l2": "inputs larger than L2 (1.26 GB of snapshots written per step)"},
                 "phases_ms": phases,
                 "online_solves_per_s": N_BATCH / ((phases["solve"] + phases["reconstruct"]) / 1e3),
+                "online_modes": online,
                 "fom_mu_per_s": n_train / (phases["fom"] / 1e3),
                 "fom_bicgstab_iters_mean": float(iters.mean()),
                 "solve_status_ok": stat_ok,

@@ -50,6 +50,7 @@ typedef int32_t st_status;
 /* Arithmetic of the reduced solve (st_options.precision). */
 #define ST_FP64          0  /* FP64 assembly, FP64 LU, FP64 refinement                 */
 #define ST_FP32_ASSEMBLY 1  /* FP32 assembly of Ahat^st, FP64 LU + FP64 refinement     */
+#define ST_FP32_LU       2  /* FP32 assembly and LU factors, FP64 residual refinement   */
 
 /* Opaque model handle: operator terms, bases, reduced operators, workspace. */
 typedef struct st_model st_model;
@@ -71,7 +72,7 @@ typedef struct {
                              largest column norm of the incoming block       (1e-12)  */
     double  eps_sv;       /* drop singular values < eps_sv * sigma_max       (1e-14)  */
     int32_t r_max;        /* rank cap of the incremental SVD                 (256)    */
-    int32_t precision;    /* ST_FP64 or ST_FP32_ASSEMBLY                     (FP64)   */
+    int32_t precision;    /* ST_FP64, ST_FP32_ASSEMBLY or ST_FP32_LU         (FP64)   */
     int64_t spin_limit;   /* polls of any device-side wait before it gives up
                              with ST_ERR_TIMEOUT (one poll ~ 0.1 us)         (2e7)    */
     int32_t refine_steps; /* iterative-refinement steps of the reduced solve (1)      */
@@ -99,6 +100,12 @@ int64_t st_kernel_launches(void);
  * Errors: ST_ERR_ARG (bad CSR), ST_ERR_OOM, ST_ERR_CUDA. */
 st_status st_model_create(const st_affine_csr* A, const st_options* opt, void* stream,
                           st_model** out);
+
+/* Replace the model's options (validated as in st_model_create); later calls
+ * use them, e.g. a different precision or refinement count for st_rom_solve.
+ * r_max changes take effect at the next st_rom_build_basis.  ST_ERR_ARG if
+ * invalid (the old options stay). */
+st_status st_model_set_options(st_model* m, const st_options* opt);
 
 /* Release every resource of the model (synchronises its stream first). */
 void st_model_destroy(st_model* m);

@@ -13,6 +13,7 @@ from .binding import (  # noqa: F401
     ST_ERR_STATE,
     ST_ERR_TIMEOUT,
     ST_FP32_ASSEMBLY,
+    ST_FP32_LU,
     ST_FP64,
     ST_OK,
     check,

@@ -30,6 +30,7 @@ ST_ERR_TIMEOUT = 8
 ST_ERR_STATE = 9
 ST_FP64 = 0
 ST_FP32_ASSEMBLY = 1
+ST_FP32_LU = 2
 
 
 class StError(RuntimeError):
@@ -62,6 +63,7 @@ _SIGS = {
     "st_kernel_launches": (c_int64, []),
     "st_model_create": (c_int32, [POINTER(st_affine_csr), POINTER(st_options), _P, POINTER(_P)]),
     "st_model_destroy": (None, [_P]),
+    "st_model_set_options": (c_int32, [_P, POINTER(st_options)]),
     "st_sync": (c_int32, [_P]),
     "st_fom_march": (c_int32, [_P, c_int32, _P, c_int32, _P, _P, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_build_basis": (c_int32, [_P, c_int32, c_int32, _P, c_int32, c_int32, _P, _P]),
@@ -154,6 +156,14 @@ class Model:
             pass
 
     # -- C entry points ---------------------------------------------------
+    def st_model_set_options(self, **kw) -> None:
+        o = st_options()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(self.opts), ctypes.sizeof(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        check(lib.st_model_set_options(self.handle, ctypes.byref(o)))
+        self.opts = o
+
     def st_sync(self) -> None:
         check(lib.st_sync(self.handle))
 

@@ -88,6 +88,19 @@ const char* st_status_string(st_status s) {
     }
 }
 
+static bool options_valid(const st_options& o) {
+    return (o.tol > 0) && o.maxit >= 1 && o.r_max >= 1 && (o.eps_svd >= 0) && (o.eps_sv >= 0) &&
+           o.spin_limit >= 1 && o.refine_steps >= 0 && o.refine_steps <= 16 && o.jacobi_sweeps >= 1 &&
+           (o.precision == ST_FP64 || o.precision == ST_FP32_ASSEMBLY || o.precision == ST_FP32_LU);
+}
+
+st_status st_model_set_options(st_model* m, const st_options* opt) {
+    if (!m || !opt) return st_fail(ST_ERR_ARG, "st_model_set_options: NULL argument");
+    if (!options_valid(*opt)) return st_fail(ST_ERR_ARG, "st_model_set_options: invalid st_options");
+    m->opt = *opt;
+    return ST_OK;
+}
+
 static void free_basis(st_model* m) {
     cudaFree(m->d_phi);
     cudaFree(m->d_T);
@@ -154,10 +167,7 @@ st_status st_model_create(const st_affine_csr* A, const st_options* opt, void* s
     st_options o;
     st_options_default(&o);
     if (opt) o = *opt;
-    if (!(o.tol > 0) || o.maxit < 1 || o.r_max < 1 || !(o.eps_svd >= 0) || !(o.eps_sv >= 0) ||
-        o.spin_limit < 1 || o.refine_steps < 0 || o.jacobi_sweeps < 1 ||
-        (o.precision != ST_FP64 && o.precision != ST_FP32_ASSEMBLY))
-        return st_fail(ST_ERR_ARG, "invalid st_options");
+    if (!options_valid(o)) return st_fail(ST_ERR_ARG, "invalid st_options");
 
     st_model* m = new st_model();
     m->opt = o;

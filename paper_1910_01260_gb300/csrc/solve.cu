@@ -46,9 +46,10 @@ struct SolveArgs {
     int32_t* err;
 };
 
+template <typename T>
 struct Smem {
-    double* P;    // panel: nfull x nb (ld nfull)
-    double* U;    // nb x CW
+    T* P;         // panel: nfull x nb (ld nfull)
+    T* U;         // nb x CW
     double* Ah;   // ns_p x ns_p
     double* b;    // rhs
     double* x;    // solution
@@ -99,9 +100,11 @@ __device__ __forceinline__ double block_sum(double v, double* s_val) {
     return t;
 }
 
-// In-place LU with partial pivoting of A (n x n, ld n).  Returns false if a
-// zero pivot occurred (the factorisation still completes, as in LAPACK).
-__device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s_val, int* s_idx) {
+// In-place LU with partial pivoting of A (n x n, ld n), in the arithmetic of
+// T.  Returns false if a zero pivot occurred (the factorisation still
+// completes, as in LAPACK).
+template <typename T>
+__device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, double* s_val, int* s_idx) {
     bool ok = true;
     const int tid = threadIdx.x;
     for (int kb = 0; kb < n; kb += nb) {
@@ -115,7 +118,7 @@ __device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s
             double bv = -1.0;
             int bi = c;
             for (int r = c + tid; r < rp; r += NT) {
-                const double v = fabs(s.P[r + c * ld_p]);
+                const double v = fabs((double)s.P[r + c * ld_p]);
                 if (v > bv) {
                     bv = v;
                     bi = r;
@@ -127,16 +130,16 @@ __device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s
             if (tid == 0) s.piv[kb + c] = kb + pr;
             if (pr != c)
                 for (int cc = tid; cc < w; cc += NT) {
-                    const double t0 = s.P[c + cc * ld_p];
+                    const T t0 = s.P[c + cc * ld_p];
                     s.P[c + cc * ld_p] = s.P[pr + cc * ld_p];
                     s.P[pr + cc * ld_p] = t0;
                 }
             __syncthreads();
-            const double pv = s.P[c + c * ld_p];
-            if (pv == 0.0) {
+            const T pv = s.P[c + c * ld_p];
+            if (pv == (T)0) {
                 ok = false;
             } else {
-                const double inv = 1.0 / pv;
+                const T inv = (T)1 / pv;
                 for (int r = c + 1 + tid; r < rp; r += NT) s.P[r + c * ld_p] *= inv;
             }
             __syncthreads();
@@ -155,11 +158,11 @@ __device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s
         // row interchanges on the columns outside the panel, in pivot order
         for (int j = tid; j < n - w; j += NT) {
             const int jj = j < kb ? j : j + w;
-            double* colp = A + (int64_t)jj * n;
+            T* colp = A + (int64_t)jj * n;
             for (int c = 0; c < w; ++c) {
                 const int pr = s.piv[kb + c];
                 if (pr != kb + c) {
-                    const double t0 = colp[kb + c];
+                    const T t0 = colp[kb + c];
                     colp[kb + c] = colp[pr];
                     colp[pr] = t0;
                 }
@@ -176,9 +179,9 @@ __device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s
             }
             __syncthreads();
             if (tid < wc) {
-                double* u = s.U + tid * nb;
+                T* u = s.U + tid * nb;
                 for (int r = 1; r < w; ++r) {
-                    double acc = u[r];
+                    T acc = u[r];
                     for (int cc = 0; cc < r; ++cc) acc = fma(-s.P[r + cc * ld_p], u[cc], acc);
                     u[r] = acc;
                 }
@@ -190,22 +193,22 @@ __device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s
             }
             const int tx = tid & 15, ty = tid >> 4;
             for (int rt = 0; rt < r22; rt += 64) {
-                double acc[4][4];
+                T acc[4][4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int bq = 0; bq < 4; ++bq) acc[a][bq] = 0.0;
+                    for (int bq = 0; bq < 4; ++bq) acc[a][bq] = (T)0;
                 for (int cc = 0; cc < w; ++cc) {
-                    double lv[4], uv[4];
+                    T lv[4], uv[4];
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         const int rr = rt + tx + 16 * a;
-                        lv[a] = rr < r22 ? s.P[(w + rr) + cc * ld_p] : 0.0;
+                        lv[a] = rr < r22 ? s.P[(w + rr) + cc * ld_p] : (T)0;
                     }
 #pragma unroll
                     for (int bq = 0; bq < 4; ++bq) {
                         const int c2 = ty + 16 * bq;
-                        uv[bq] = c2 < wc ? s.U[cc + c2 * nb] : 0.0;
+                        uv[bq] = c2 < wc ? s.U[cc + c2 * nb] : (T)0;
                     }
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
@@ -220,7 +223,7 @@ __device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s
                     for (int bq = 0; bq < 4; ++bq) {
                         const int c2 = ty + 16 * bq;
                         if (c2 >= wc) continue;
-                        double* p = A + (kb + w + rr) + (int64_t)(j0 + c2) * n;
+                        T* p = A + (kb + w + rr) + (int64_t)(j0 + c2) * n;
                         *p -= acc[a][bq];
                     }
                 }
@@ -231,8 +234,10 @@ __device__ bool lu_factor(double* A, int n, int ld_p, int nb, Smem& s, double* s
     return ok;
 }
 
-// x <- A^{-1} x using the LU factors and pivots in A / s.piv.
-__device__ void lu_solve(const double* A, int n, Smem& s, double* x) {
+// x <- A^{-1} x using the LU factors and pivots in A / s.piv (factors in T,
+// x in FP64; with T = float the products are rounded to FP32 factors' accuracy).
+template <typename T>
+__device__ void lu_solve(const T* A, int n, Smem<T>& s, double* x) {
     const int tid = threadIdx.x;
     if (tid == 0)
         for (int i = 0; i < n; ++i) {
@@ -246,14 +251,14 @@ __device__ void lu_solve(const double* A, int n, Smem& s, double* x) {
     __syncthreads();
     for (int c = 0; c < n; ++c) {
         const double xc = x[c];
-        for (int r = c + 1 + tid; r < n; r += NT) x[r] = fma(-A[r + (int64_t)c * n], xc, x[r]);
+        for (int r = c + 1 + tid; r < n; r += NT) x[r] = fma(-(double)A[r + (int64_t)c * n], xc, x[r]);
         __syncthreads();
     }
     for (int c = n - 1; c >= 0; --c) {
-        if (tid == 0) x[c] /= A[c + (int64_t)c * n];
+        if (tid == 0) x[c] /= (double)A[c + (int64_t)c * n];
         __syncthreads();
         const double xc = x[c];
-        for (int r = tid; r < c; r += NT) x[r] = fma(-A[r + (int64_t)c * n], xc, x[r]);
+        for (int r = tid; r < c; r += NT) x[r] = fma(-(double)A[r + (int64_t)c * n], xc, x[r]);
         __syncthreads();
     }
 }
@@ -271,21 +276,24 @@ __device__ __forceinline__ double st_entry(const SolveArgs& g, const double* Ah,
     return v;
 }
 
+// T: arithmetic of the assembled matrix and its LU factors (double, or
+// float for the FP32-factorisation mode); residuals and the solution are FP64.
+template <typename T>
 __global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
     extern __shared__ double smem[];
     __shared__ double s_val[NWARP];
     __shared__ int s_idx[NWARP];
     __shared__ int s_item;
     const int nfull = g.nfull, nb = g.nb;
-    Smem s;
-    s.P = smem;
+    Smem<T> s;
+    s.P = reinterpret_cast<T*>(smem);
     s.U = s.P + (size_t)nfull * nb;
-    s.Ah = s.U + (size_t)nb * CW;
+    s.Ah = reinterpret_cast<double*>(s.U + (size_t)nb * CW);
     s.b = s.Ah + (size_t)g.ns * g.ns;
     s.x = s.b + nfull;
     s.r = s.x + nfull;
     s.piv = reinterpret_cast<int*>(s.r + nfull);
-    double* A = g.ws + (size_t)blockIdx.x * nfull * nfull;
+    T* A = reinterpret_cast<T*>(g.ws) + (size_t)blockIdx.x * nfull * nfull;
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) {
@@ -327,7 +335,7 @@ __global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
         // assemble Ahat^st (FP64, or FP32 products in the FP32-assembly mode)
         for (int64_t t = tid; t < (int64_t)n * n; t += NT) {
             const int row = (int)(t % n), col = (int)(t / n);
-            double v;
+            T v;
             if (g.fp32_asm) {
                 const int ip = row % a, jp = row / a, i = col % a, j = col / a;
                 const int64_t gi = (int64_t)(ip + g.ns * jp) + (int64_t)(i + g.ns * j) * nfull;
@@ -336,9 +344,9 @@ __global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
                     const int64_t mi = (int64_t)i * g.nt * g.nt + jp + (int64_t)j * g.nt;
                     f += (float)(g.M[mi] - g.S[mi]);
                 }
-                v = (double)f;
+                v = (T)f;
             } else {
-                v = st_entry(g, s.Ah, a, row, col);
+                v = (T)st_entry(g, s.Ah, a, row, col);
             }
             A[row + (int64_t)col * n] = v;
         }
@@ -420,6 +428,65 @@ __global__ void size_scatter_kernel(int n_mu, const int* __restrict__ npv, int* 
         order[atomicAdd(hist + npv[p], 1)] = p;
 }
 
+// Dynamic shared memory of solve_kernel<T> for panel width nb.
+size_t solve_smem(int nfull, int ns, int nb, size_t tsize) {
+    return tsize * ((size_t)nfull * nb + (size_t)nb * CW) +
+           sizeof(double) * ((size_t)ns * ns + 3 * (size_t)nfull) + sizeof(int) * (size_t)nfull + 64;
+}
+
+bool fp32_factors(const st_model* m) { return m->opt.precision == ST_FP32_LU; }
+
+
+// Shared-memory plan and grid for solve_kernel<T>; the panel width shrinks if
+// a wide model does not fit.
+template <typename T>
+st_status solve_plan(st_model* m, int cap_per_sm, int* nb_out, size_t* smem_out, int* blocks_out) {
+    const int ns = m->ns, nfull = ns * m->nt;
+    int nb = 32;
+    int max_optin = 0;
+    ST_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+    while (nb > 4 && solve_smem(nfull, ns, nb, sizeof(T)) > (size_t)max_optin) nb /= 2;
+    const size_t smem = solve_smem(nfull, ns, nb, sizeof(T));
+    if (smem > (size_t)max_optin) return st_fail(ST_ERR_ARG, "st_rom_solve: ns*nt = %d too large", nfull);
+    ST_CUDA_TRY(cudaFuncSetAttribute(solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel<T>, NT, smem));
+    *nb_out = nb;
+    *smem_out = smem;
+    *blocks_out = std::max(1, std::min(per_sm, cap_per_sm)) * m->num_sms;
+    return ST_OK;
+}
+
+SolveArgs solve_args(st_model* m, int n_mu, const double* theta, const int32_t* ns_nt, double* uhat,
+                     double* rel_res, int32_t* status, const int* order, unsigned int* queue,
+                     double* ws, int nb) {
+    SolveArgs g;
+    g.n_mu = n_mu;
+    g.Q = m->Q;
+    g.ns = m->ns;
+    g.nt = m->nt;
+    g.nfull = m->ns * m->nt;
+    g.Ahat = m->d_Ahat;
+    g.G = m->d_G;
+    g.G32 = m->d_G32;
+    g.M = m->d_M;
+    g.S = m->d_S;
+    g.rhs = m->d_rhs;
+    g.theta = theta;
+    g.ns_nt = ns_nt;
+    g.order = order;
+    g.queue = queue;
+    g.uhat = uhat;
+    g.rel_res = rel_res;
+    g.status = status;
+    g.ws = ws;
+    g.refine = m->opt.refine_steps;
+    g.fp32_asm = m->opt.precision == ST_FP32_ASSEMBLY || m->opt.precision == ST_FP32_LU;
+    g.nb = nb;
+    g.err = m->d_err;
+    return g;
+}
+
 }  // namespace
 
 extern "C" st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta,
@@ -431,25 +498,17 @@ extern "C" st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta
     if (n_mu == 0) return ST_OK;
     const int ns = m->ns, nt = m->nt, nfull = ns * nt;
     cudaStream_t st = m->stream;
-    // shared-memory plan: the panel width shrinks if a wide model does not fit
-    int nb = 32;
-    auto smem_for = [&](int b) {
-        return sizeof(double) * ((size_t)nfull * b + (size_t)b * CW + (size_t)ns * ns + 3 * (size_t)nfull) +
-               sizeof(int) * (size_t)nfull + 64;
-    };
-    int max_optin = 0;
-    ST_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
-    while (nb > 4 && smem_for(nb) > (size_t)max_optin) nb /= 2;
-    const size_t smem = smem_for(nb);
-    if (smem > (size_t)max_optin) return st_fail(ST_ERR_ARG, "st_rom_solve: ns*nt = %d too large", nfull);
-    ST_CUDA_TRY(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, NT, smem));
-    const int blocks = std::max(1, std::min(per_sm, 2)) * m->num_sms;
+    const bool f32 = fp32_factors(m);
+    const size_t tsize = f32 ? sizeof(float) : sizeof(double);
+    int nb = 0, blocks = 0;
+    size_t smem = 0;
+    if (f32) ST_TRY(solve_plan<float>(m, 4, &nb, &smem, &blocks));
+    else ST_TRY(solve_plan<double>(m, 2, &nb, &smem, &blocks));
     const size_t ints = (size_t)2 * n_mu + nfull + 1 + 16;
-    ST_TRY(st_grow(m, m->ws_solve, sizeof(double) * (size_t)blocks * nfull * nfull + sizeof(int) * ints));
+    const size_t ws_bytes = ((tsize * (size_t)blocks * nfull * nfull) + 255) / 256 * 256;
+    ST_TRY(st_grow(m, m->ws_solve, ws_bytes + sizeof(int) * ints));
     double* ws = (double*)m->ws_solve.p;
-    int* npv = (int*)(ws + (size_t)blocks * nfull * nfull);
+    int* npv = (int*)((char*)m->ws_solve.p + ws_bytes);
     int* order = npv + n_mu;
     int* hist = order + n_mu;
     ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
@@ -459,31 +518,9 @@ extern "C" st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta
     size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
     ST_TRY(st_check_launch("solve order"));
     ST_CUDA_TRY(cudaMemsetAsync(m->d_bar + 3, 0, sizeof(unsigned int), st));
-    SolveArgs g;
-    g.n_mu = n_mu;
-    g.Q = m->Q;
-    g.ns = ns;
-    g.nt = nt;
-    g.nfull = nfull;
-    g.Ahat = m->d_Ahat;
-    g.G = m->d_G;
-    g.G32 = m->d_G32;
-    g.M = m->d_M;
-    g.S = m->d_S;
-    g.rhs = m->d_rhs;
-    g.theta = theta;
-    g.ns_nt = ns_nt;
-    g.order = order;
-    g.queue = m->d_bar + 3;
-    g.uhat = uhat;
-    g.rel_res = rel_res;
-    g.status = status;
-    g.ws = ws;
-    g.refine = m->opt.refine_steps;
-    g.fp32_asm = m->opt.precision == ST_FP32_ASSEMBLY;
-    g.nb = nb;
-    g.err = m->d_err;
-    solve_kernel<<<blocks, NT, smem, st>>>(g);
+    SolveArgs g = solve_args(m, n_mu, theta, ns_nt, uhat, rel_res, status, order, m->d_bar + 3, ws, nb);
+    if (f32) solve_kernel<float><<<blocks, NT, smem, st>>>(g);
+    else solve_kernel<double><<<blocks, NT, smem, st>>>(g);
     return st_check_launch("solve");
 }
 
@@ -558,23 +595,14 @@ extern "C" st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double
                        "st_rom_solve_static: n_mu = %d with ns*nt = %d needs %zu bytes of scratch, "
                        "more than the fixed %zu",
                        n_mu, nfull, int_bytes + mat_bytes, kStaticScratchBytes);
-    int nb = 32;
-    auto smem_for = [&](int b) {
-        return sizeof(double) * ((size_t)nfull * b + (size_t)b * CW + (size_t)ns * ns + 3 * (size_t)nfull) +
-               sizeof(int) * (size_t)nfull + 64;
-    };
-    int max_optin = 0;
-    ST_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
-    while (nb > 4 && smem_for(nb) > (size_t)max_optin) nb /= 2;
-    const size_t smem = smem_for(nb);
-    if (smem > (size_t)max_optin)
-        return st_fail(ST_ERR_ARG, "st_rom_solve_static: ns*nt = %d too large", nfull);
-    ST_CUDA_TRY(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, NT, smem));
-    const size_t fit = (kStaticScratchBytes - int_bytes) / mat_bytes;
-    const int blocks = (int)std::max<size_t>(
-        1, std::min<size_t>(fit, (size_t)std::max(1, std::min(per_sm, 2)) * m->num_sms));
+    const bool f32 = fp32_factors(m);
+    const size_t mat_t = (f32 ? sizeof(float) : sizeof(double)) * (size_t)nfull * nfull;
+    int nb = 0, cap_blocks = 0;
+    size_t smem = 0;
+    if (f32) ST_TRY(solve_plan<float>(m, 4, &nb, &smem, &cap_blocks));
+    else ST_TRY(solve_plan<double>(m, 2, &nb, &smem, &cap_blocks));
+    const size_t fit = (kStaticScratchBytes - int_bytes) / mat_t;
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>(fit, (size_t)cap_blocks));
     unsigned char* sb = static_cast<unsigned char*>(base);
     unsigned int* queue = reinterpret_cast<unsigned int*>(sb);
     int* npv = reinterpret_cast<int*>(sb) + 16;
@@ -589,30 +617,8 @@ extern "C" st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double
     size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
     size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
     ST_TRY(st_check_launch("solve_static order"));
-    SolveArgs g;
-    g.n_mu = n_mu;
-    g.Q = m->Q;
-    g.ns = ns;
-    g.nt = nt;
-    g.nfull = nfull;
-    g.Ahat = m->d_Ahat;
-    g.G = m->d_G;
-    g.G32 = m->d_G32;
-    g.M = m->d_M;
-    g.S = m->d_S;
-    g.rhs = m->d_rhs;
-    g.theta = theta;
-    g.ns_nt = ns_nt;
-    g.order = order;
-    g.queue = queue;
-    g.uhat = uhat;
-    g.rel_res = rel_res;
-    g.status = status;
-    g.ws = ws;
-    g.refine = m->opt.refine_steps;
-    g.fp32_asm = m->opt.precision == ST_FP32_ASSEMBLY;
-    g.nb = nb;
-    g.err = m->d_err;
-    solve_kernel<<<blocks, NT, smem, st>>>(g);
+    SolveArgs g = solve_args(m, n_mu, theta, ns_nt, uhat, rel_res, status, order, queue, ws, nb);
+    if (f32) solve_kernel<float><<<blocks, NT, smem, st>>>(g);
+    else solve_kernel<double><<<blocks, NT, smem, st>>>(g);
     return st_check_launch("solve_static");
 }

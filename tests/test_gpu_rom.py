@@ -68,10 +68,12 @@ def _solve(m, thetas, sizes, n_full):
     return uhat.cpu().numpy(), res.cpu().numpy(), status.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_batched_solve_uneven_sizes(c1_model, precision):
+    # precision 1: FP32 assembly; 2: FP32 assembly and LU factors.  The FP64
+    # residual refinement brings both back to the FP64 tolerance.
     p, ref, rm = c1_model
-    m = _gpu_model(p, ref, p.ns, p.nt, precision=precision, refine_steps=2 if precision else 1)
+    m = _gpu_model(p, ref, p.ns, p.nt, precision=precision, refine_steps=(1, 2, 3)[precision])
     rng = np.random.default_rng(11)
     n = 300
     mus = p.mu_lo + rng.random((n, 2)) * (p.mu_hi - p.mu_lo)
@@ -137,4 +139,19 @@ def test_reconstruction_and_outputs(c1_model):
         want = strom.reconstruct(ref["Phi_s"], ref["T"], uh[k, :a * b], p.ns, a, b)
         assert rel_max(U[k].T, want) < 1e-13
         assert rel_max(Y[k].T, Cout.T @ want) < 1e-12
+    m.close()
+
+
+def test_set_options_switches_precision(c1_model):
+    import paper_1910_01260_gb300 as st
+    p, ref, rm = c1_model
+    m = _gpu_model(p, ref, p.ns, p.nt)
+    th = p.theta(p.test_mu)
+    a, _, _ = _solve(m, th, None, p.ns * p.nt)
+    m.st_model_set_options(precision=st.ST_FP32_LU, refine_steps=3)
+    b, res, status = _solve(m, th, None, p.ns * p.nt)
+    assert (status == 0).all() and res.max() < 1e-12
+    assert rel_max(b, a) < 1e-10
+    with pytest.raises(st.StError):
+        m.st_model_set_options(precision=7)
     m.close()
