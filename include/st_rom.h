@@ -244,6 +244,51 @@ st_status st_rom_reconstruct(st_model* m, int32_t n_mu, const double* uhat,
                              const int32_t* ns_nt, double* u, int32_t n_out, const double* Cout,
                              double* y);
 
+/* Learned surrogate mu -> uhat (no counterpart in the paper; it serves the
+ * many-query use the paper motivates): a 3-layer MLP 2 -> 256 -> 256 -> ns*nt
+ * with exact-erf GELU, FP32 master weights, BF16 copies on the tensor cores,
+ * FP32 accumulation and outputs.  The input is mu mapped affinely from the box
+ * [mu_lo, mu_hi] onto [-1, 1]^2; the targets are the FP64 reduced solutions
+ * uhat normalised per component by their mean and standard deviation.
+ * Training: Adam (0.9, 0.999, eps 1e-8, bias correction) with cosine decay of
+ * lr over all steps; each epoch visits the samples in the order
+ * i -> (a i + c) mod n, with a, c from SplitMix64 keyed by (seed, epoch), in
+ * minibatches of `batch`.  Synchronous.
+ *   mu     dev [n x 2] parameters, uhat dev [n x ns*nt] targets (full basis)
+ *   mu_lo, mu_hi host [2] parameter box
+ *   init   host [count] initial FP32 parameters (W1, b1, W2, b2, W3, b3, row
+ *          major [out x in]) or NULL for Kaiming-uniform from seed
+ *   epoch_loss host [epochs] or NULL: mean training loss of each epoch
+ * Requires a basis; ns*nt must be a multiple of 8. */
+st_status st_rom_surrogate_train(st_model* m, int32_t n, const double* mu, const double* mu_lo,
+                                 const double* mu_hi, const double* uhat, const float* init,
+                                 int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                                 float* epoch_loss);
+
+/* Surrogate inference gated by the reduced space-time residual: every
+ * prediction is accepted if ||Ahat^st(mu) uhat - rhs|| / ||rhs|| <= gate
+ * (evaluated in FP32 from the affine pieces of Ahat^st, Eq. ij-block-matrix),
+ * otherwise the sample is solved by the batched FP64 LU of st_rom_solve.
+ *   mu dev [n x 2], theta dev [n x Q] (same samples), uhat dev [n x ns*nt]
+ *   rel_res dev [n]: gate residual, or the LU residual for fallback samples
+ *   used_fallback dev [n]: 1 where the LU was used
+ *   n_fallback host or NULL: number of fallback samples (synchronises). */
+st_status st_rom_surrogate_infer(st_model* m, int32_t n, const double* mu, const double* theta,
+                                 double gate, double* uhat, double* rel_res, int32_t* used_fallback,
+                                 int32_t* n_fallback);
+
+/* Current FP32 surrogate parameters (host [count], layout as for init);
+ * params may be NULL to query count.  Synchronous. */
+st_status st_rom_surrogate_params(st_model* m, float* params, int64_t* count);
+
+/* Loss and gradients of the surrogate loss at the given parameters on one
+ * batch (targets normalised with the batch's own statistics), for checking the
+ * backward kernels.  grad host [count] or NULL, loss host or NULL.
+ * Synchronous; leaves the surrogate untrained. */
+st_status st_rom_surrogate_loss_grad(st_model* m, int32_t n, const double* mu, const double* mu_lo,
+                                     const double* mu_hi, const double* uhat, const float* params,
+                                     float* grad, float* loss);
+
 #ifdef __cplusplus
 }
 #endif

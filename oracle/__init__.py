@@ -13,4 +13,4 @@ closed form, an identity the paper states, a library routine used as an
 independent solver, or brute force on tiny inputs, except where a docstring
 says "parity unpinned".
 """
-from . import fom, pod, strom  # noqa: F401
+from . import fom, mlp, pod, strom  # noqa: F401

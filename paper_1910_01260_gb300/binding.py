@@ -75,6 +75,11 @@ _SIGS = {
     "st_rom_solve": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_solve_static": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_reconstruct": (c_int32, [_P, c_int32, _P, _P, _P, c_int32, _P, _P]),
+    "st_rom_surrogate_train": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P, c_int32, c_int32, ctypes.c_float,
+                                         ctypes.c_uint64, _P]),
+    "st_rom_surrogate_infer": (c_int32, [_P, c_int32, _P, _P, c_double, _P, _P, _P, _P]),
+    "st_rom_surrogate_params": (c_int32, [_P, _P, _P]),
+    "st_rom_surrogate_loss_grad": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -228,3 +233,47 @@ class Model:
     def st_rom_reconstruct(self, n_mu, uhat, ns_nt, u=None, n_out=0, Cout=None, y=None) -> None:
         check(lib.st_rom_reconstruct(self.handle, n_mu, ptr(uhat), ptr(ns_nt), ptr(u), n_out,
                                      ptr(Cout), ptr(y)))
+
+
+def _surrogate_methods():
+    def st_rom_surrogate_train(self, n, mu, mu_lo, mu_hi, uhat, init=None, epochs=100, batch=1024,
+                               lr=1e-3, seed=5):
+        lo = _host(mu_lo, np.float64)
+        hi = _host(mu_hi, np.float64)
+        ini = None if init is None else _host(init, np.float32)
+        losses = np.zeros(max(int(epochs), 1), dtype=np.float32)
+        self._keep = [lo, hi, ini, losses]
+        check(lib.st_rom_surrogate_train(self.handle, n, ptr(mu), ptr(lo), ptr(hi), ptr(uhat), ptr(ini),
+                                         epochs, batch, ctypes.c_float(lr), ctypes.c_uint64(seed),
+                                         ptr(losses)))
+        return losses[:epochs].copy()
+
+    def st_rom_surrogate_infer(self, n, mu, theta, gate, uhat, rel_res, used_fallback):
+        nf = np.zeros(1, dtype=np.int32)
+        check(lib.st_rom_surrogate_infer(self.handle, n, ptr(mu), ptr(theta), gate, ptr(uhat), ptr(rel_res),
+                                         ptr(used_fallback), ptr(nf)))
+        return int(nf[0])
+
+    def st_rom_surrogate_params(self):
+        cnt = np.zeros(1, dtype=np.int64)
+        check(lib.st_rom_surrogate_params(self.handle, None, ptr(cnt)))
+        out = np.zeros(int(cnt[0]), dtype=np.float32)
+        check(lib.st_rom_surrogate_params(self.handle, ptr(out), ptr(cnt)))
+        return out
+
+    def st_rom_surrogate_loss_grad(self, n, mu, mu_lo, mu_hi, uhat, params):
+        lo = _host(mu_lo, np.float64)
+        hi = _host(mu_hi, np.float64)
+        pr = _host(params, np.float32)
+        grad = np.zeros_like(pr)
+        loss = np.zeros(1, dtype=np.float32)
+        check(lib.st_rom_surrogate_loss_grad(self.handle, n, ptr(mu), ptr(lo), ptr(hi), ptr(uhat), ptr(pr),
+                                             ptr(grad), ptr(loss)))
+        return float(loss[0]), grad
+
+    for f in (st_rom_surrogate_train, st_rom_surrogate_infer, st_rom_surrogate_params,
+              st_rom_surrogate_loss_grad):
+        setattr(Model, f.__name__, f)
+
+
+_surrogate_methods()

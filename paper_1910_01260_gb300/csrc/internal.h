@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libst_rom.so.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -63,6 +64,16 @@ struct st_model {
 
     // scratch buffers (grown on demand, reused across calls)
     DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_solve, ws_misc;
+
+    // learned surrogate mu -> uhat (3-layer MLP, FP32 masters, BF16 copies)
+    struct Mlp {
+        int n_in = 2, hidden = 256, n_out = 0;
+        int64_t n_params = 0;
+        bool trained = false;
+        int64_t adam_t = 0;
+        double lo[2] = {0, 0}, hi[2] = {1, 1};
+        DevBuf params, grad, adam_m, adam_v, wbf, stats, act, kall, list;
+    } mlp;
 };
 
 // ---- error handling -------------------------------------------------------
@@ -112,3 +123,9 @@ st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nco
 // Release basis (and reduced operators) / reduced operators only.
 void st_internal_free_basis(st_model* m);
 void st_internal_free_reduced(st_model* m);
+
+// Solve the reduced systems of the samples listed in list[0..n_list) (full
+// (ns, nt) of the model) with the batched LU kernel; same outputs as
+// st_rom_solve for those samples.
+st_status st_internal_solve_list(st_model* m, int n_list, const int* list, const double* theta,
+                                 double* uhat, double* rel_res, int32_t* status);

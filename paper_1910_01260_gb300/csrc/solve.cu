@@ -524,6 +524,27 @@ extern "C" st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta
     return st_check_launch("solve");
 }
 
+st_status st_internal_solve_list(st_model* m, int n_list, const int* list, const double* theta,
+                                 double* uhat, double* rel_res, int32_t* status) {
+    if (n_list <= 0) return ST_OK;
+    const int nfull = m->ns * m->nt;
+    cudaStream_t st = m->stream;
+    const bool f32 = fp32_factors(m);
+    const size_t tsize = f32 ? sizeof(float) : sizeof(double);
+    int nb = 0, blocks = 0;
+    size_t smem = 0;
+    if (f32) ST_TRY(solve_plan<float>(m, 4, &nb, &smem, &blocks));
+    else ST_TRY(solve_plan<double>(m, 2, &nb, &smem, &blocks));
+    const size_t ws_bytes = ((tsize * (size_t)blocks * nfull * nfull) + 255) / 256 * 256;
+    ST_TRY(st_grow(m, m->ws_solve, ws_bytes + sizeof(int) * 16));
+    ST_CUDA_TRY(cudaMemsetAsync(m->d_bar + 3, 0, sizeof(unsigned int), st));
+    SolveArgs g = solve_args(m, n_list, theta, nullptr, uhat, rel_res, status, list, m->d_bar + 3,
+                             (double*)m->ws_solve.p, nb);
+    if (f32) solve_kernel<float><<<blocks, NT, smem, st>>>(g);
+    else solve_kernel<double><<<blocks, NT, smem, st>>>(g);
+    return st_check_launch("solve_list");
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free variant of st_rom_solve.
 //

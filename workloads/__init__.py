@@ -17,4 +17,6 @@ from .transport import (  # noqa: F401
     uniform_mu,
     c4_batch,
     c5_samples,
+    mlp_init,
+    mu_to_input,
 )

@@ -349,3 +349,29 @@ def c5_samples(n_train: int = 8192, n_infer: int = 65536, prob: Optional[Problem
     lo = np.array([0.5, 0.1]) if prob is None else prob.mu_lo
     hi = np.array([1.5, 0.95]) if prob is None else prob.mu_hi
     return uniform_mu(n_train, lo, hi, 5), uniform_mu(n_infer, lo, hi, 6)
+
+
+# ---------------------------------------------------------------------------
+# Surrogate network inputs: seeded initial weights and the mapping of mu to
+# the network input.  (Random draws of the method are inputs to both sides.)
+# ---------------------------------------------------------------------------
+
+MLP_HIDDEN = 256
+
+
+def mlp_init(n_out: int, hidden: int = MLP_HIDDEN, n_in: int = 2, seed: int = 5):
+    """Kaiming-uniform weights (bound sqrt(6 / fan_in)) and zero biases for
+    the 3-layer network n_in -> hidden -> hidden -> n_out.  Returns a list of
+    (W [out x in], b [out]) float64 arrays."""
+    rng = np.random.default_rng(seed)
+    dims = [n_in, hidden, hidden, n_out]
+    out = []
+    for a, b in zip(dims[:-1], dims[1:]):
+        bound = math.sqrt(6.0 / a)
+        out.append((rng.uniform(-bound, bound, (b, a)), np.zeros(b)))
+    return out
+
+
+def mu_to_input(mu: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    """Affine map of the parameter box onto [-1, 1]^2."""
+    return 2.0 * (np.asarray(mu) - lo) / (hi - lo) - 1.0
