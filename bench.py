@@ -197,6 +197,84 @@ def run_reference(args, rank: int, world: int) -> None:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def run_surrogate(m, prob, B, stream, args) -> dict:
+    """c5: MLP 2->256->256->480 trained on 8192 ROM solutions at (40, 12),
+    inference on 65,536 parameters gated at 1e-4 with LU fallback."""
+    import torch
+
+    import paper_1910_01260_gb300 as st
+    from workloads import c5_samples
+    dev = B.device
+    n_full = prob.ns * prob.nt
+    mu_tr, mu_inf = c5_samples(8192, 65536, prob)
+    th_tr = torch.tensor(prob.theta(mu_tr), device=dev)
+    th_inf = torch.tensor(prob.theta(mu_inf), device=dev)
+    mu_tr_d = torch.tensor(mu_tr, device=dev)
+    mu_inf_d = torch.tensor(mu_inf, device=dev)
+    u_tr = torch.zeros((len(mu_tr), n_full), dtype=torch.float64, device=dev)
+    m.st_model_set_options(precision=st.ST_FP32_LU, refine_steps=3)
+    m.st_rom_solve(len(mu_tr), th_tr, None, u_tr)
+    m.st_sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev[0].record(stream)
+    losses = m.st_rom_surrogate_train(len(mu_tr), mu_tr_d, prob.mu_lo, prob.mu_hi, u_tr, epochs=args.sur_epochs,
+                                      batch=1024, lr=2e-3, seed=5)
+    ev[1].record(stream)
+    n = len(mu_inf)
+    uh = torch.zeros((n, n_full), dtype=torch.float64, device=dev)
+    rr = torch.zeros(n, dtype=torch.float64, device=dev)
+    used = torch.zeros(n, dtype=torch.int32, device=dev)
+    m.st_rom_surrogate_infer(n, mu_inf_d, th_inf, 1e-4, uh, rr, used)   # warm
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    nf = m.st_rom_surrogate_infer(n, mu_inf_d, th_inf, 1e-4, uh, rr, used)
+    ev[3].record(stream)
+    u_lu = torch.zeros_like(uh)
+    r_lu = torch.zeros_like(rr)
+    m.st_rom_solve(n, th_inf, None, u_lu, r_lu)
+    torch.cuda.synchronize()
+    ev[4].record(stream)
+    m.st_rom_solve(n, th_inf, None, u_lu, r_lu)
+    ev[5].record(stream)
+    torch.cuda.synchronize()
+    t_train = ev[0].elapsed_time(ev[1])
+    t_inf = ev[2].elapsed_time(ev[3])
+    t_lu = ev[4].elapsed_time(ev[5])
+    # pure surrogate (no fallback) accuracy against the LU solutions
+    uh_free = torch.zeros_like(uh)
+    e6 = torch.cuda.Event(enable_timing=True)
+    e7 = torch.cuda.Event(enable_timing=True)
+    e6.record(stream)
+    m.st_rom_surrogate_infer(n, mu_inf_d, th_inf, 1e30, uh_free, rr, used)
+    e7.record(stream)
+    torch.cuda.synchronize()
+    t_free = e6.elapsed_time(e7)
+    err = (torch.linalg.norm(uh_free - u_lu, dim=1) / torch.linalg.norm(u_lu, dim=1)).cpu().numpy()
+    gate_res = rr.cpu().numpy()
+    rates = {f"{g:g}": float(np.mean(gate_res > g)) for g in (1e-4, 1e-3, 1e-2, 1e-1)}
+    # surrogate prediction against the FOM at a few inference parameters
+    sel = np.arange(4)
+    fsn = torch.empty((len(sel), prob.Nt, prob.N), dtype=torch.float64, device=dev)
+    m.st_fom_march(prob.theta(mu_inf[sel]), prob.dt, None, B, prob.F, fsn)
+    ur = torch.zeros_like(fsn)
+    m.st_rom_reconstruct(len(sel), uh_free[sel].contiguous(), None, ur)
+    ul = torch.zeros_like(fsn)
+    m.st_rom_reconstruct(len(sel), u_lu[sel].contiguous(), None, ul)
+    m.st_sync()
+    e_sur = max(float(torch.linalg.norm(fsn[j] - ur[j]) / torch.linalg.norm(fsn[j])) for j in range(len(sel)))
+    e_lu = max(float(torch.linalg.norm(fsn[j] - ul[j]) / torch.linalg.norm(fsn[j])) for j in range(len(sel)))
+    m.st_model_set_options(precision=st.ST_FP64, refine_steps=1)
+    return {"workload": "c5: MLP 2->256->256->480 on the (40,12) model; 8192 training ROM solutions, 65536 inference",
+            "train_ms": t_train, "epochs": args.sur_epochs, "batch": 1024, "loss_first": float(losses[0]),
+            "loss_last": float(losses[-1]), "gate": 1e-4, "n_infer": n, "n_fallback_at_gate": nf,
+            "fallback_rate_at_gate": nf / n, "gated_infer_ms": t_inf, "gated_solves_per_s": n / (t_inf / 1e3),
+            "lu_only_ms": t_lu, "lu_only_solves_per_s": n / (t_lu / 1e3),
+            "surrogate_and_gate_ms": t_free, "surrogate_and_gate_per_s": n / (t_free / 1e3),
+            "fallback_rate_by_gate": rates, "median_rel_err_vs_lu_ungated": float(np.median(err)),
+            "p99_rel_err_vs_lu_ungated": float(np.quantile(err, 0.99)),
+            "rel_err_vs_fom_sampled": {"surrogate_ungated": e_sur, "lu": e_lu}}
+
+
 def run_gpu(args, rank: int, world: int, dist) -> None:
     import torch
 
@@ -349,6 +427,11 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     uhat.copy_(ref_uhat)
     m.st_sync()
 
+    # ---- learned surrogate (c5): train on ROM solutions, gated inference --
+    surrogate = None
+    if not args.no_surrogate:
+        surrogate = run_surrogate(m, prob, B, stream, args)
+
     # ---- accuracy of the ROM against the FOM on sampled batch parameters -
     acc = {}
     sel = []
@@ -401,6 +484,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                 "phases_ms": phases,
                 "online_solves_per_s": N_BATCH / ((phases["solve"] + phases["reconstruct"]) / 1e3),
                 "online_modes": online,
+                "surrogate": surrogate,
                 "fom_mu_per_s": n_train / (phases["fom"] / 1e3),
                 "fom_bicgstab_iters_mean": float(iters.mean()),
                 "solve_status_ok": stat_ok,
@@ -424,6 +508,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--r-max", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-epochs", type=int, default=200)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -309,10 +309,7 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
     int sweep = 0;
     bool converged = false;
     for (; sweep < a.max_sweeps; ++sweep) {
-        if (blockIdx.x == 0 && tid == 0) {
-            a.flags[(sweep + 1) % 3] = 0;
-            if (sweep == 0) a.nrm2[a.n] = 0.0;
-        }
+        if (blockIdx.x == 0 && tid == 0) a.flags[(sweep + 1) % 3] = 0;
         for (int c = gw; c < a.n; c += nw) {
             const double* xc = a.X + (int64_t)c * a.ldx;
             double acc = 0.0;
@@ -703,6 +700,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         ST_TRY(st_check_launch("eye"));
         ST_CUDA_TRY(cudaMemsetAsync(d_int + 3, 0, sizeof(int) * 3, st));
         ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
+        // the largest squared column norm is accumulated with atomicMax from zero
+        ST_CUDA_TRY(cudaMemsetAsync(d_sig_tmp + ncols, 0, sizeof(double), st));
         {
             const int npairs = (ncols + 1) / 2;
             int jb = std::max(1, std::min(jac_blocks_max, npairs));
