@@ -50,6 +50,25 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
 
 
+def aggregate(local_ms: float, units_per_rank: int, dist, device=None):
+    """Max-over-ranks step time and the whole-job throughput (units of all
+    ranks / that time).  Replicas: every rank processes its own units and
+    nothing but the timing scalar is exchanged."""
+    world = dist.get_world_size() if dist is not None else 1
+    ms = local_ms
+    if dist is not None:
+        import torch
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms / 1e3)
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Each replica solves its own seeded batch (weak scaling)."""
+    return base + rank
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -288,7 +307,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     prob = problem_for("c4")
     N, Nt, ns, nt = prob.N, prob.Nt, prob.ns, prob.nt
     n_full = ns * nt
-    mu_b, sizes = c4_batch(N_BATCH, prob, seed=4 + rank)
+    mu_b, sizes = c4_batch(N_BATCH, prob, seed=rank_seed(4, rank))
     theta_train = prob.theta(prob.train_mu)
     theta_b = prob.theta(mu_b)
     n_train = theta_train.shape[0]
@@ -355,13 +374,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     launches = st.lib.st_kernel_launches() - launches0
     clk = clocks.stop()
     m.st_sync()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    ms_step = elapsed_ms / args.steps
-    value = world * N_BATCH / (ms_step / 1e3)
+    ms_step, value = aggregate(t_start.elapsed_time(t_end) / args.steps, N_BATCH, dist, dev)
     phases = {k: float(np.mean(v)) for k, v in phase_ms.items()}
     iters = f_iters.cpu().numpy()
     stat_ok = int((s_status == 0).sum().item())
@@ -395,12 +408,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * N_BATCH / (e2e_ms / 1e3)
+    e2e_ms, e2e_value = aggregate(e0.elapsed_time(e1) / args.steps, N_BATCH, dist, dev)
 
     # ---- online phase alone, per precision mode (same model and batch) ---
     online = {}
@@ -500,6 +508,66 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     m.close()
 
 
+def run_case(case: str) -> None:
+    """One small workload of a single kernel family, for profiling with ncu.
+    fom: FOM march of the 16 training parameters, 10 steps (one launch);
+    pod: full-size snapshots, then the incremental POD;
+    solve: seeded (40,12) bases, the 4096-parameter batch in FP64 and FP32-LU;
+    mlp: surrogate forward (tcgen05 GEMMs) on 65,536 parameters."""
+    import torch
+
+    import paper_1910_01260_gb300 as st
+    from workloads import c4_batch, c5_samples, problem_for
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    prob = problem_for("c4")
+    m = st.Model(prob.rowptr, prob.col, prob.vals, st.options(), stream=stream.cuda_stream)
+    B = torch.tensor(prob.B.T.copy(), device=dev)
+    n_train = len(prob.train_mu)
+    if case in ("fom", "pod"):
+        Nt = 10 if case == "fom" else prob.Nt
+        snaps = torch.empty((n_train, Nt, prob.N), dtype=torch.float64, device=dev)
+        m.st_fom_march(prob.theta(prob.train_mu), prob.dt[:Nt], None, B, prob.F[:Nt], snaps)
+        if case == "pod":
+            m.st_rom_build_basis(n_train, Nt, snaps, prob.ns, prob.nt)
+    else:
+        rng = np.random.default_rng(1)
+        Phi = np.linalg.qr(rng.standard_normal((prob.N, prob.ns)))[0]
+        T = np.zeros((prob.Nt, prob.ns * prob.nt))
+        for i in range(prob.ns):
+            T[:, i::prob.ns] = np.linalg.qr(rng.standard_normal((prob.Nt, prob.nt)))[0]
+        m.st_model_set_basis(prob.ns, prob.nt, prob.Nt, torch.tensor(Phi.T.copy(), device=dev),
+                             torch.tensor(T.T.copy(), device=dev))
+        m.st_rom_assemble(prob.dt, B, prob.F, None)
+        nf = prob.ns * prob.nt
+        if case == "solve":
+            mu, sizes = c4_batch(N_BATCH, prob)
+            th = torch.tensor(prob.theta(mu), device=dev)
+            sz = torch.tensor(sizes, device=dev)
+            uh = torch.zeros((N_BATCH, nf), dtype=torch.float64, device=dev)
+            m.st_rom_solve(N_BATCH, th, sz, uh)
+            m.st_model_set_options(precision=st.ST_FP32_LU, refine_steps=3)
+            m.st_rom_solve(N_BATCH, th, sz, uh)
+        elif case == "mlp":
+            mu_tr, mu_inf = c5_samples(2048, 65536, prob)
+            th_tr = torch.tensor(prob.theta(mu_tr), device=dev)
+            u_tr = torch.zeros((len(mu_tr), nf), dtype=torch.float64, device=dev)
+            m.st_rom_solve(len(mu_tr), th_tr, None, u_tr)
+            m.st_rom_surrogate_train(len(mu_tr), torch.tensor(mu_tr, device=dev), prob.mu_lo, prob.mu_hi, u_tr,
+                                     epochs=2, batch=1024)
+            n = len(mu_inf)
+            uh = torch.zeros((n, nf), dtype=torch.float64, device=dev)
+            rr = torch.zeros(n, dtype=torch.float64, device=dev)
+            used = torch.zeros(n, dtype=torch.int32, device=dev)
+            m.st_rom_surrogate_infer(n, torch.tensor(mu_inf, device=dev), torch.tensor(prob.theta(mu_inf), device=dev),
+                                     1e30, uh, rr, used)
+        else:
+            raise SystemExit(f"unknown case {case}")
+    m.st_sync()
+    m.close()
+    print(f"case {case} ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,7 +578,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=200)
+    ap.add_argument("--case", default=None, help="run one small profiling workload: fom, pod, solve, mlp")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
