@@ -362,6 +362,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = st.lib.st_kernel_launches()
+    m.st_profile_enable(True)
     barrier()
     t_start.record(stream)
     for _ in range(args.steps):
@@ -374,6 +375,10 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     launches = st.lib.st_kernel_launches() - launches0
     clk = clocks.stop()
     m.st_sync()
+    prof = m.st_profile_read()
+    m.st_profile_enable(False)
+    pod_sweeps, pod_reorth = m.st_pod_get_stats()
+    pod_sigma, pod_rank = m.st_pod_get_state()
     ms_step, value = aggregate(t_start.elapsed_time(t_end) / args.steps, N_BATCH, dist, dev)
     phases = {k: float(np.mean(v)) for k, v in phase_ms.items()}
     iters = f_iters.cpu().numpy()
@@ -464,17 +469,32 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     n = sizes[:, 0].astype(np.float64) * sizes[:, 1]
     refine = 1
     solve_flops = float(np.sum((2.0 / 3.0) * n ** 3 + (refine + 1) * 4.0 * n ** 2 + refine * 2.0 * n ** 2 + 4 * n ** 2))
-    kern = {
-        "fom_march_kernel": {"ms": phases["fom"], "flops": fom_flops},
-        "solve_kernel": {"ms": phases["solve"], "flops": solve_flops},
-    }
-    for k in kern.values():
-        k["achieved_tflops"] = k["flops"] / (k["ms"] * 1e-3) / 1e12
-        k["frac"] = k["achieved_tflops"] / FP64_PEAK_TFLOPS
-    dom = max(kern, key=lambda k: kern[k]["ms"])
-    roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["achieved_tflops"],
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kern[dom]["frac"],
-            "traffic": None, "peak_source": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz"}
+    # per-kernel device time over the timed steps (CUDA events recorded by the
+    # library around each launch on this stream); algorithmic flops from the
+    # library where it can count them on the host, else from this workload
+    host_flops = {"fom_march_kernel": fom_flops * args.steps,
+                  "solve_kernel<double>": solve_flops * args.steps}
+    total_ms = sum(v[0] for v in prof.values())
+    kern = {}
+    for name, (ms, nl, fl) in prof.items():
+        fl = fl or host_flops.get(name, 0.0)
+        k = {"ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps,
+             "share": ms / total_ms if total_ms else 0.0}
+        if fl:
+            k["gflop_per_launch"] = fl / nl / 1e9
+            k["achieved_tflops"] = fl / (ms * 1e-3) / 1e12
+            k["frac_fp64"] = k["achieved_tflops"] / FP64_PEAK_TFLOPS
+        kern[name] = k
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom].get("achieved_tflops"),
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kern[dom].get("frac_fp64"),
+            "traffic": None, "launch_ms": kern[dom]["ms_per_step"] / kern[dom]["launches_per_step"],
+            "peak_source": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz"}
+    sig = np.asarray(pod_sigma)
+    pod_diag = {"rank": pod_rank, "updates": len(pod_sweeps), "jacobi_sweeps": pod_sweeps,
+                "reorthogonalisations": pod_reorth,
+                "sigma_rel": {str(i): float(sig[i] / sig[0]) for i in (1, 10, 20, 40, 80, 160, 255)
+                              if i < len(sig)}}
 
     if rank == 0:
         cpu = None
@@ -498,6 +518,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                 "solve_status_ok": stat_ok,
                 "rom_rel_err_vs_fom": acc,
                 "kernels": kern,
+                "pod": pod_diag,
                 "roofline": roof,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
@@ -530,6 +551,20 @@ def run_case(case: str) -> None:
         m.st_fom_march(prob.theta(prob.train_mu), prob.dt[:Nt], None, B, prob.F[:Nt], snaps)
         if case == "pod":
             m.st_rom_build_basis(n_train, Nt, snaps, prob.ns, prob.nt)
+            m.st_sync()
+            m.st_profile_enable(True)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            sig, rank = m.st_rom_build_basis(n_train, Nt, snaps, prob.ns, prob.nt)
+            t1.record(stream)
+            m.st_sync()
+            sweeps, reorth = m.st_pod_get_stats()
+            prof = m.st_profile_read()
+            m.st_profile_enable(False)
+            print(json.dumps({"pod_ms": t0.elapsed_time(t1), "rank": rank, "sweeps": sweeps, "reorth": reorth,
+                              "sigma_rel": [float(sig[i] / sig[0]) for i in range(0, len(sig), 16)],
+                              "kernels": {k: [round(v[0], 3), v[1], v[2]] for k, v in prof.items()}}))
     else:
         rng = np.random.default_rng(1)
         Phi = np.linalg.qr(rng.standard_normal((prob.N, prob.ns)))[0]

@@ -171,6 +171,33 @@ st_status st_model_get_basis(st_model* m, double* phi_s, double* T, int32_t* dim
  * NULL, r host or NULL. */
 st_status st_pod_get_state(st_model* m, double* W, double* V, double* sigma, int32_t* r);
 
+/* Per-kernel timing.  st_profile_enable(m, 1) makes every later call on the
+ * model record a pair of CUDA events on the model's stream around each of
+ * its kernel launches (a few microseconds of overhead per launch);
+ * st_profile_enable(m, 0) stops it.  Either call synchronises the stream
+ * and clears the totals.  st_profile_read synchronises and returns, for each
+ * kernel name seen since the last enable, sorted by total time (largest
+ * first): names [cap x ST_PROFILE_NAME_LEN] NUL-terminated, ms [cap] total
+ * milliseconds, launches [cap], flops [cap] the algorithmic floating-point
+ * operations the library can count on the host (2MNK per GEMM; norms, dot
+ * products and 6(m + n) per applied rotation in the middle-matrix Jacobi
+ * SVD; 0 where the count depends on device-side data); any of the four may
+ * be NULL.  *n_kernels receives the number of names (which may exceed cap).
+ * A name covers one kernel, or a kernel with its small helper (the split-K
+ * reduction of a GEMM, the size sort of a batched solve). */
+#define ST_PROFILE_NAME_LEN 64
+st_status st_profile_enable(st_model* m, int32_t on);
+st_status st_profile_read(st_model* m, int32_t cap, char* names, double* ms, int64_t* launches,
+                          double* flops, int32_t* n_kernels);
+
+/* Diagnostics of the last st_rom_build_basis (host, synchronous): the number
+ * of block updates in *n_updates; the one-sided Jacobi sweeps of each
+ * update's middle-matrix SVD in sweeps[0 .. min(n_updates, cap) - 1] (sweeps
+ * may be NULL); the number of updates whose orthogonality check fired and
+ * re-orthogonalised W in *n_reorth (may be NULL). */
+st_status st_pod_get_stats(st_model* m, int32_t* n_updates, int32_t* sweeps, int32_t cap,
+                           int32_t* n_reorth);
+
 /* Offline assembly of the space-time reduced operators through the block
  * structure of Sec. 4.3, never forming Phi_st:
  *   Ahat_q = Phi_s^T A_q Phi_s           (reduced system matrix, Eq. galerkin)

@@ -31,6 +31,7 @@ ST_ERR_STATE = 9
 ST_FP64 = 0
 ST_FP32_ASSEMBLY = 1
 ST_FP32_LU = 2
+PROFILE_NAME_LEN = 64
 
 
 class StError(RuntimeError):
@@ -70,6 +71,9 @@ _SIGS = {
     "st_model_set_basis": (c_int32, [_P, c_int32, c_int32, c_int32, _P, _P]),
     "st_model_get_basis": (c_int32, [_P, _P, _P, _P]),
     "st_pod_get_state": (c_int32, [_P, _P, _P, _P, _P]),
+    "st_pod_get_stats": (c_int32, [_P, _P, _P, c_int32, _P]),
+    "st_profile_enable": (c_int32, [_P, c_int32]),
+    "st_profile_read": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_assemble": (c_int32, [_P, _P, c_int32, _P, _P, _P]),
     "st_model_get_reduced": (c_int32, [_P, _P, _P, _P, _P, _P]),
     "st_rom_solve": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
@@ -202,6 +206,35 @@ class Model:
         sig = np.zeros(max(int(r[0]), 1), dtype=np.float64)
         check(lib.st_pod_get_state(self.handle, ptr(W), ptr(V), ptr(sig), ptr(r)))
         return sig[:r[0]].copy(), int(r[0])
+
+    def st_pod_get_stats(self):
+        """(Jacobi sweeps per block update, number of W re-orthogonalisations)."""
+        n = np.zeros(1, dtype=np.int32)
+        check(lib.st_pod_get_stats(self.handle, ptr(n), None, 0, None))
+        sw = np.zeros(max(int(n[0]), 1), dtype=np.int32)
+        ro = np.zeros(1, dtype=np.int32)
+        check(lib.st_pod_get_stats(self.handle, ptr(n), ptr(sw), int(n[0]), ptr(ro)))
+        return sw[:n[0]].tolist(), int(ro[0])
+
+    def st_profile_enable(self, on: bool = True) -> None:
+        check(lib.st_profile_enable(self.handle, 1 if on else 0))
+
+    def st_profile_read(self):
+        """{kernel name: (total ms, launches, algorithmic flops or 0)} since the
+        last st_profile_enable, largest total time first."""
+        n = np.zeros(1, dtype=np.int32)
+        check(lib.st_profile_read(self.handle, 0, None, None, None, None, ptr(n)))
+        k = int(n[0])
+        names = np.zeros((max(k, 1), PROFILE_NAME_LEN), dtype=np.uint8)
+        ms = np.zeros(max(k, 1), dtype=np.float64)
+        cnt = np.zeros(max(k, 1), dtype=np.int64)
+        fl = np.zeros(max(k, 1), dtype=np.float64)
+        check(lib.st_profile_read(self.handle, k, ptr(names), ptr(ms), ptr(cnt), ptr(fl), ptr(n)))
+        out = {}
+        for i in range(min(k, int(n[0]))):
+            name = bytes(names[i]).split(b"\0", 1)[0].decode()
+            out[name] = (float(ms[i]), int(cnt[i]), float(fl[i]))
+        return out
 
     def st_rom_assemble(self, dt, B, F, u0=None) -> None:
         dth = _host(dt, np.float64)

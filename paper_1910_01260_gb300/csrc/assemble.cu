@@ -141,9 +141,12 @@ extern "C" st_status st_rom_assemble(st_model* m, const double* dt, int32_t n_in
     {
         dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 127) / 128, 4 * m->num_sms)),
                   (unsigned)(Q * ((ns + CB - 1) / CB)));
-        spmm_kernel<<<grid, 128, 0, st>>>(N, m->d_slice_ptr, m->d_slice_w, m->d_col, m->d_vals,
-                                          m->ell_size, ns, m->d_phi, Y);
-        ST_TRY(st_check_launch("spmm"));
+        {
+            ST_PROF(m, "spmm_kernel");
+            spmm_kernel<<<grid, 128, 0, st>>>(N, m->d_slice_ptr, m->d_slice_w, m->d_col, m->d_vals,
+                                              m->ell_size, ns, m->d_phi, Y);
+            ST_TRY(st_check_launch("spmm"));
+        }
         for (int q = 0; q < Q; ++q)
             ST_TRY(st_dgemm(m, true, false, ns, ns, N, 1.0, m->d_phi, N, Y + (size_t)q * N * ns, N, 0.0,
                             m->d_Ahat + (size_t)q * ns * ns, ns));

@@ -36,29 +36,59 @@ __device__ __forceinline__ void grid_abort(const GridBarrier& b, int32_t code) {
     atomicExch(b.abort, 1u);
 }
 
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(unsigned int* p, unsigned int v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_release_gpu(unsigned int* p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA co-resident).  The
+// CTA's writes are ordered before its arrival by the block barrier and the
+// release of the arrival atomic; the last CTA to arrive resets the counter
+// and releases the generation word, on which the others spin with acquire
+// loads.  The spin is bounded: past `limit` polls the kernel records
+// ST_ERR_TIMEOUT and raises the abort flag; a CTA that sees the abort flag
+// stops waiting.  Returns false after an abort or a timeout (a CTA that
+// aborts returns without arriving, so the others never complete the barrier).
 __device__ __forceinline__ bool grid_sync(const GridBarrier& b, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = b.gen;
-        unsigned int my = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(b.count, 1u);
+        const unsigned int my = ld_acquire_gpu(b.gen);
+        const unsigned int arrived = atom_add_acq_rel_gpu(b.count, 1u);
+        int ok = 1;
         if (arrived == gridDim.x - 1) {
-            atomicExch(b.count, 0u);
-            __threadfence();
-            atomicAdd(b.gen, 1u);
+            st_relaxed_gpu(b.count, 0u);
+            red_release_gpu(b.gen, 1u);
         } else {
             long long it = 0;
-            while (*vgen == my) {
-                if (++it > b.limit || *(volatile unsigned int*)b.abort) {
-                    if (it > b.limit) grid_abort(b, ST_ERR_TIMEOUT);
+            while (ld_acquire_gpu(b.gen) == my) {
+                if (++it > b.limit) {
+                    grid_abort(b, ST_ERR_TIMEOUT);
+                    ok = 0;
                     break;
                 }
-                __nanosleep(100);
+                if (*(volatile unsigned int*)b.abort) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
             }
         }
-        __threadfence();
-        *s_flag = (*(volatile unsigned int*)b.abort == 0u);
+        *s_flag = ok;
     }
     __syncthreads();
     return *s_flag != 0;

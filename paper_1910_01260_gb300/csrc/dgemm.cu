@@ -139,6 +139,8 @@ st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nc,
               (unsigned)(batch * std::max(splits, 1)));
     if (grid.y > 65535 || grid.z > 65535) return st_fail(ST_ERR_ARG, "st_dgemm: grid too large");
     int sp = std::max(splits, 1);
+    ST_PROF(m, "dgemm_kernel");
+    st_prof_flops(m, "dgemm_kernel", 2.0 * (double)M * (double)Nc * (double)K * (double)batch);
 #define ST_LAUNCH(ta, tb)                                                                   \
     dgemm_kernel<ta, tb><<<grid, NT, 0, m->stream>>>(M, Nc, K, kchunk, alpha, A, lda, sA, B, \
                                                      ldb, sB, beta, C, ldc, sC, sp, ws)

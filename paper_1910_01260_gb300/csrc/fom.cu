@@ -517,9 +517,12 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     double* vecs = amu + (size_t)ell * LD;
     double* partial = vecs + 7 * vec;
     int sblocks = (int)std::min<int64_t>((ell * LD + 255) / 256, 8 * m->num_sms);
-    fom_setup_kernel<LD><<<std::max(sblocks, 1), 256, 0, m->stream>>>(
-        ell, m->Q, m->d_vals, d_theta, n_mu, amu, N, u0, vecs);
-    ST_TRY(st_check_launch("fom_setup"));
+    {
+        ST_PROF(m, "fom_setup_kernel");
+        fom_setup_kernel<LD><<<std::max(sblocks, 1), 256, 0, m->stream>>>(
+            ell, m->Q, m->d_vals, d_theta, n_mu, amu, N, u0, vecs);
+        ST_TRY(st_check_launch("fom_setup"));
+    }
     ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, m->stream));
     FomArgs a;
     a.N = N;
@@ -548,6 +551,7 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     a.maxit = m->opt.maxit;
     a.bar = GridBarrier{m->d_bar, m->d_bar + 1, m->d_bar + 2, m->d_err, m->opt.spin_limit};
     void* args[] = {&a};
+    ST_PROF(m, "fom_march_kernel");
     ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)fom_march_kernel<LD>, dim3(blocks), dim3(NT),
                                             args, 0, m->stream));
         st_count_launch();

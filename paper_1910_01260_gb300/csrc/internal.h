@@ -21,6 +21,22 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Per-kernel timing (st_profile_enable): CUDA events recorded around each
+// launch on the model's stream, read back by st_profile_read.
+struct ProfState {
+    bool on = false;
+    struct Rec {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<int64_t> launches;
+    std::vector<double> flops;
+};
+
 struct st_model {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -47,6 +63,11 @@ struct st_model {
     int64_t pod_rows = 0;
     DevBuf W, V;
     std::vector<double> sigma;
+    // per block update of the last basis build: middle-matrix Jacobi sweeps,
+    // and the number of Gram-Schmidt re-orthogonalisations of W
+    std::vector<int> pod_sweeps;
+    int pod_reorth = 0;
+    ProfState prof;
 
     // reduced operators
     bool assembled = false;
@@ -99,6 +120,20 @@ st_status st_fail(st_status code, const char* fmt, ...);
 // releasing a smaller buffer that queued work may still use.
 st_status st_grow(st_model* m, DevBuf& buf, size_t bytes);
 st_status st_check_launch(const char* what);
+// Scope timer: while profiling is on, records an event pair around the
+// launches made inside the scope, attributed to `name` (a string literal).
+struct ProfScope {
+    st_model* m;
+    const char* name;
+    cudaEvent_t a = nullptr;
+    ProfScope(st_model* model, const char* kernel);
+    ~ProfScope();
+};
+#define ST_PROF_CAT2(a, b) a##b
+#define ST_PROF_CAT(a, b) ST_PROF_CAT2(a, b)
+// Add algorithmic flops to a kernel's profile entry (no-op unless profiling).
+void st_prof_flops(st_model* m, const char* name, double flops);
+#define ST_PROF(m, name) ProfScope ST_PROF_CAT(st_prof_scope_, __LINE__)((m), (name))
 // Count one kernel launch (st_check_launch counts the launch it checks).
 void st_count_launch();
 

@@ -618,12 +618,18 @@ extern "C" st_status st_rom_surrogate_infer(st_model* m, int32_t n, const double
         denorm_kernel<<<grid1d(m, (int64_t)bb * n_out), NT, 0, st>>>(bb, n_out, a.Y, v.mean, v.stdv,
                                                                      uhat + (int64_t)b0 * n_out, n_out);
         ST_TRY(st_check_launch("mlp denorm"));
-        gate_gemm_kernel<<<dim3((R + 63) / 64, (bb + 63) / 64), 256, 0, st>>>(bb, R, n_out, uhat + (int64_t)b0 * n_out,
-                                                                             n_out, (float*)s.kall.p, C);
-        ST_TRY(st_check_launch("mlp gate gemm"));
-        gate_kernel<<<bb, 128, 0, st>>>(bb, b0, n_out, Q, C, theta + (int64_t)b0 * Q, m->d_rhs, gate, rel_res + b0,
-                                       used_fallback + b0, list, count);
-        ST_TRY(st_check_launch("mlp gate"));
+        {
+            ST_PROF(m, "gate_gemm_kernel");
+            gate_gemm_kernel<<<dim3((R + 63) / 64, (bb + 63) / 64), 256, 0, st>>>(
+                bb, R, n_out, uhat + (int64_t)b0 * n_out, n_out, (float*)s.kall.p, C);
+            ST_TRY(st_check_launch("mlp gate gemm"));
+        }
+        {
+            ST_PROF(m, "gate_kernel");
+            gate_kernel<<<bb, 128, 0, st>>>(bb, b0, n_out, Q, C, theta + (int64_t)b0 * Q, m->d_rhs, gate,
+                                           rel_res + b0, used_fallback + b0, list, count);
+            ST_TRY(st_check_launch("mlp gate"));
+        }
     }
     unsigned int hc = 0;
     ST_CUDA_TRY(cudaMemcpyAsync(&hc, count, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));

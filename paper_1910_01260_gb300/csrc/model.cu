@@ -53,6 +53,71 @@ st_status st_check_launch(const char* what) {
     return ST_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Per-kernel timing
+static cudaEvent_t prof_event(st_model* m) {
+    cudaEvent_t e = nullptr;
+    if (!m->prof.pool.empty()) {
+        e = m->prof.pool.back();
+        m->prof.pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+ProfScope::ProfScope(st_model* model, const char* kernel) : m(model), name(kernel) {
+    if (!m || !m->prof.on) {
+        m = nullptr;
+        return;
+    }
+    a = prof_event(m);
+    if (a) cudaEventRecord(a, m->stream);
+}
+
+ProfScope::~ProfScope() {
+    if (!m || !a) return;
+    cudaEvent_t b = prof_event(m);
+    if (!b) {
+        m->prof.pool.push_back(a);
+        return;
+    }
+    cudaEventRecord(b, m->stream);
+    m->prof.pending.push_back({name, a, b});
+}
+
+static size_t prof_slot(ProfState& p, const char* name) {
+    size_t i = 0;
+    while (i < p.names.size() && p.names[i] != name) ++i;
+    if (i == p.names.size()) {
+        p.names.emplace_back(name);
+        p.ms.push_back(0.0);
+        p.launches.push_back(0);
+        p.flops.push_back(0.0);
+    }
+    return i;
+}
+
+void st_prof_flops(st_model* m, const char* name, double flops) {
+    if (!m || !m->prof.on) return;
+    m->prof.flops[prof_slot(m->prof, name)] += flops;
+}
+
+static void prof_collect(st_model* m) {
+    ProfState& p = m->prof;
+    for (const ProfState::Rec& r : p.pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            const size_t i = prof_slot(p, r.name);
+            p.ms[i] += ms;
+            p.launches[i] += 1;
+        }
+        p.pool.push_back(r.a);
+        p.pool.push_back(r.b);
+    }
+    p.pending.clear();
+}
+
 extern "C" {
 
 void st_options_default(st_options* o) {
@@ -121,12 +186,52 @@ static void free_reduced(st_model* m) {
     m->assembled = false;
 }
 
+st_status st_profile_enable(st_model* m, int32_t on) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_profile_enable: NULL model");
+    ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    prof_collect(m);
+    m->prof.names.clear();
+    m->prof.ms.clear();
+    m->prof.launches.clear();
+    m->prof.flops.clear();
+    m->prof.on = on != 0;
+    return ST_OK;
+}
+
+st_status st_profile_read(st_model* m, int32_t cap, char* names, double* ms, int64_t* launches,
+                          double* flops, int32_t* n_kernels) {
+    if (!m || !n_kernels || cap < 0) return st_fail(ST_ERR_ARG, "st_profile_read: bad arguments");
+    ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    prof_collect(m);
+    const ProfState& p = m->prof;
+    std::vector<int> order(p.names.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return p.ms[x] > p.ms[y]; });
+    *n_kernels = (int32_t)order.size();
+    for (int i = 0; i < (int)order.size() && i < cap; ++i) {
+        const int k = order[i];
+        if (names) {
+            std::strncpy(names + (size_t)i * ST_PROFILE_NAME_LEN, p.names[k].c_str(), ST_PROFILE_NAME_LEN - 1);
+            names[(size_t)i * ST_PROFILE_NAME_LEN + ST_PROFILE_NAME_LEN - 1] = '\0';
+        }
+        if (ms) ms[i] = p.ms[k];
+        if (launches) launches[i] = p.launches[k];
+        if (flops) flops[i] = p.flops[k];
+    }
+    return ST_OK;
+}
+
 void st_model_destroy(st_model* m) {
     if (!m) return;
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(m->device);
     cudaStreamSynchronize(m->stream);
+    for (const ProfState::Rec& r : m->prof.pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : m->prof.pool) cudaEventDestroy(e);
     free_basis(m);
     free_reduced(m);
     cudaFree(m->d_slice_ptr);
@@ -300,6 +405,16 @@ st_status st_pod_get_state(st_model* m, double* W, double* V, double* sigma, int
                                     cudaMemcpyDeviceToDevice, m->stream));
     if (sigma) std::memcpy(sigma, m->sigma.data(), sizeof(double) * m->pod_r);
     ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return ST_OK;
+}
+
+st_status st_pod_get_stats(st_model* m, int32_t* n_updates, int32_t* sweeps, int32_t cap,
+                           int32_t* n_reorth) {
+    if (!m || !n_updates || cap < 0) return st_fail(ST_ERR_ARG, "st_pod_get_stats: bad arguments");
+    *n_updates = (int32_t)m->pod_sweeps.size();
+    if (sweeps)
+        for (int i = 0; i < (int)m->pod_sweeps.size() && i < cap; ++i) sweeps[i] = m->pod_sweeps[i];
+    if (n_reorth) *n_reorth = m->pod_reorth;
     return ST_OK;
 }
 

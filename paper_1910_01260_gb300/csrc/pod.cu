@@ -12,8 +12,10 @@
 //      that directions normalised from small remainders lose the rounding
 //      they carried along W; L = L1 + L2 P1, P = P2 P1;
 //   3. bordered middle matrix Q = [[diag(sigma), L], [0, P]] (Eq. middleMat),
-//      thin SVD by one-sided (Hestenes) Jacobi in FP64 on Q^T, with rotations
-//      accumulated to give the left singular vectors of Q;
+//      thin SVD in FP64, preconditioned one-sided Jacobi: pivoted Householder
+//      QR Q^T Pi = Q1 R, one-sided (Hestenes) Jacobi on R^T with the
+//      rotations accumulated in Y, so Q = (Pi U_z) Sigma (Q1 Y)^T with U_z
+//      the normalised Jacobi columns (the QR cuts the sweeps about 2.5x);
 //   4. W <- [W J] Ubar, V <- blkdiag(V, I) Vbar, sigma <- Sigma_bar, dropping
 //      sigma < eps_sv * sigma_max and keeping at most r_max;
 //   5. orthogonality check |w_1^T w_r| > min(eps_svd, eps N) and, if it fires,
@@ -253,12 +255,212 @@ __global__ void eye_kernel(int n, double* Y, int ldy) {
 }
 
 // ---------------------------------------------------------------------------
-// One-sided Jacobi on the columns of X (m x n), rotations accumulated into Y
-// (n x n).  Round-robin ordering: every round pairs each column once, a
-// sweep of n_p - 1 rounds meets every pair.  One warp per pair and one warp
-// per block, so the pairs of a round spread over all SMs (the rotations are
-// FP64-throughput bound).  Squared column norms are kept in nrm2 and updated
-// with each rotation; they are recomputed at the start of every sweep.
+// Householder QR with column pivoting of X (m x n, m >= n), in place and
+// without moving columns: logical column k of X Pi is physical column
+// piv[k].  Step k picks the unused column with the largest trailing norm
+// (smallest index on ties), builds the reflector H_k = I - tau_k v v^T that
+// maps its rows k..m-1 to beta_k e_k (v_k = 1, v_i = x_i / (x_k - beta_k)),
+// and applies H_k to every other unused column.  The pivot column keeps its
+// pre-reflection rows k..m-1 (from which v is rebuilt) and rows 0..k-1 hold
+// R(0:k, k); R(k, k) = beta_k.  Columns are owned by CTAs (j mod grid), so a
+// step needs one grid barrier; the trailing norms are recomputed exactly and
+// double buffered, -1 marking pivoted columns.  Used as the preconditioner of
+// the one-sided Jacobi SVD: Jacobi on R^T needs far fewer sweeps than on X.
+struct QrpArgs {
+    int m, n;
+    double* X;
+    int ldx;
+    double* beta;   // [n]
+    double* tau;    // [n]
+    double* scale;  // [n] 1 / (x_k - beta_k), 0 for a zero column
+    int* piv;       // [n]
+    double* nrm;    // [2 n]
+    GridBarrier bar;
+};
+
+constexpr int QT = 256;
+constexpr int QW = QT / 32;
+
+__global__ void __launch_bounds__(QT) qrp_kernel(QrpArgs a) {
+    extern __shared__ double qv[];  // [m] pivot column, then the reflector
+    __shared__ double s_val[QW];
+    __shared__ int s_idx[QW];
+    __shared__ int s_p, s_flag;
+    __shared__ double s_tau, s_scale;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, b = blockIdx.x;
+    // squared norms of the owned columns (warp per column)
+    {
+        int cnt = 0;
+        for (int j = b; j < a.n; j += G, ++cnt) {
+            if (cnt % QW != warp) continue;
+            const double* x = a.X + (int64_t)j * a.ldx;
+            double s = 0.0;
+            for (int i = lane; i < a.m; i += 32) {
+                const double v = __ldcg(x + i);
+                s = fma(v, v, s);
+            }
+            s = warp_sum(s);
+            if (lane == 0) __stcg(a.nrm + j, s);
+        }
+    }
+    if (!grid_sync(a.bar, &s_flag)) return;
+    for (int k = 0; k < a.n; ++k) {
+        const double* nin = a.nrm + (size_t)(k & 1) * a.n;
+        double* nout = a.nrm + (size_t)((k + 1) & 1) * a.n;
+        // pivot: largest trailing norm, smallest index on ties
+        double bv = -1.0;
+        int bi = a.n;
+        for (int j = tid; j < a.n; j += QT) {
+            const double v = __ldcg(nin + j);
+            if (v > bv) {
+                bv = v;
+                bi = j;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            s_val[warp] = bv;
+            s_idx[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double v = s_val[0];
+            int p = s_idx[0];
+            for (int w = 1; w < QW; ++w)
+                if (s_val[w] > v || (s_val[w] == v && s_idx[w] < p)) {
+                    v = s_val[w];
+                    p = s_idx[w];
+                }
+            s_p = p;
+        }
+        __syncthreads();
+        const int p = s_p;
+        // pivot column rows k..m-1 and its norm
+        const double* xp = a.X + (int64_t)p * a.ldx;
+        double s = 0.0;
+        for (int i = k + tid; i < a.m; i += QT) {
+            const double v = __ldcg(xp + i);
+            qv[i] = v;
+            s = fma(v, v, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) s_val[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < QW; ++w) t += s_val[w];
+            const double alpha = qv[k], nx = sqrt(t);
+            double beta = 0.0, tau = 0.0, sc = 0.0;
+            if (nx > 0.0) {
+                beta = -copysign(nx, alpha);
+                tau = (beta - alpha) / beta;
+                sc = 1.0 / (alpha - beta);
+            }
+            s_tau = tau;
+            s_scale = sc;
+            if (b == 0) {
+                a.beta[k] = beta;
+                a.tau[k] = tau;
+                a.scale[k] = sc;
+                a.piv[k] = p;
+            }
+        }
+        __syncthreads();
+        const double sc = s_scale, tau = s_tau;
+        for (int i = k + 1 + tid; i < a.m; i += QT) qv[i] *= sc;
+        if (tid == 0) qv[k] = 1.0;
+        __syncthreads();
+        // apply H_k to the owned unused columns, new trailing norms
+        int cnt = 0;
+        for (int j = b; j < a.n; j += G, ++cnt) {
+            if (cnt % QW != warp) continue;
+            const double nj = __ldcg(nin + j);
+            if (j == p || nj < 0.0) {
+                if (lane == 0) __stcg(nout + j, -1.0);
+                continue;
+            }
+            double* x = a.X + (int64_t)j * a.ldx;
+            double w = 0.0;
+            for (int i = k + lane; i < a.m; i += 32) w = fma(qv[i], __ldcg(x + i), w);
+            w = warp_sum(w) * tau;
+            double s2 = 0.0;
+            for (int i = k + lane; i < a.m; i += 32) {
+                const double v = fma(-w, qv[i], __ldcg(x + i));
+                __stcg(x + i, v);
+                if (i > k) s2 = fma(v, v, s2);
+            }
+            s2 = warp_sum(s2);
+            if (lane == 0) __stcg(nout + j, s2);
+        }
+        if (!grid_sync(a.bar, &s_flag)) return;
+    }
+}
+
+// Z = R^T (n x n, lower triangular) from the in-place pivoted QR, and Y = I.
+__global__ void build_rt_kernel(int n, const double* __restrict__ X, int ldx, const int* __restrict__ piv,
+                                const double* __restrict__ beta, double* Z, int ldz, double* Y, int ldy) {
+    const int64_t tot = (int64_t)n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t % n), i = (int)(t / n);  // Z[c, i] = R[i, c]
+        double v = 0.0;
+        if (i < c) v = X[i + (int64_t)piv[c] * ldx];
+        else if (i == c) v = beta[c];
+        Z[c + (int64_t)i * ldz] = v;
+        Y[c + (int64_t)i * ldy] = c == i ? 1.0 : 0.0;
+    }
+}
+
+// B (m x nc) <- Q1 B = H_0 H_1 ... H_{n-1} B: the reflectors of qrp_kernel
+// in reverse order, one warp per column of B, each reflector staged once per
+// CTA in shared memory.
+__global__ void __launch_bounds__(128) apply_q_kernel(int m, int n, int nc, const double* __restrict__ X,
+                                                      int ldx, const int* __restrict__ piv,
+                                                      const double* __restrict__ tau,
+                                                      const double* __restrict__ scale, double* B, int ldb) {
+    extern __shared__ double v[];  // [m]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c = blockIdx.x * nw + warp;
+    double* bc = B + (int64_t)c * ldb;
+    for (int k = n - 1; k >= 0; --k) {
+        const double t = tau[k];
+        if (t == 0.0) continue;
+        const double* x = X + (int64_t)piv[k] * ldx;
+        const double sc = scale[k];
+        __syncthreads();
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) v[i] = i == k ? 1.0 : x[i] * sc;
+        __syncthreads();
+        if (c < nc) {
+            double w = 0.0;
+            for (int i = k + lane; i < m; i += 32) w = fma(v[i], bc[i], w);
+            w = warp_sum(w) * t;
+            for (int i = k + lane; i < m; i += 32) bc[i] = fma(-w, v[i], bc[i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi on the columns of X (m x n), rotations
+// accumulated into Y (n x n), cyclic by blocks.  The columns, visited in
+// decreasing-norm order each sweep, are grouped into blocks of KB; a
+// round-robin tournament over the blocks gives each CTA a pair of blocks per
+// round.  The CTA stages those 2 KB columns of X and Y in shared memory and
+// rotates every cross pair (block I column against block J column) in KB
+// inner rounds of KB disjoint pairs, one pair per JW / KB warps; in a sweep's
+// first round the pairs inside each block are rotated as well.  Every pair of
+// columns is thus met once per sweep, as in the classical cyclic ordering,
+// with one grid barrier per block round instead of one per column round.
+// Squared column norms are carried with the rotations and recomputed at the
+// start of every sweep.  The sweep loop stops after a sweep without rotation.
 struct JacArgs {
     int m, n;
     double* X;
@@ -271,7 +473,7 @@ struct JacArgs {
     int* sweeps;   // out
     double* nrm2;  // [n + 1]: squared column norms, then the largest
     double cut;    // relative singular-value cut below which columns are dropped
-    int* perm;     // [n] visiting order of the current sweep
+    unsigned long long* rotations;  // out: rotations applied (accumulated)
     GridBarrier bar;
 };
 
@@ -285,40 +487,57 @@ __device__ __forceinline__ void jacobi_pair_rot(double alpha, double beta, doubl
     s = c * t;
 }
 
-constexpr int JW = 4;  // warps per Jacobi pair (one pair per block)
+constexpr int JW = 4;  // warps per Jacobi CTA
+#ifndef ST_JACOBI_KB
+#define ST_JACOBI_KB 2
+#endif
+constexpr size_t kJacobiSmemMax = 200 * 1024;
 
-__device__ __forceinline__ double jac_block_sum(double v, double* s_red) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < JW; ++w) t += s_red[w];
-    __syncthreads();
-    return t;
+// Round-robin tournament of np (even) players: round t, table q -> (i, j).
+__device__ __forceinline__ void rr_pair(int np, int t, int q, int& i, int& j) {
+    if (q == 0) {
+        i = t;
+        j = np - 1;
+    } else {
+        i = (t + q) % (np - 1);
+        j = (t - q + np - 1) % (np - 1);
+    }
 }
 
+template <int KB>
 __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
+    constexpr int NC = 2 * KB;     // columns staged per block pair
+    constexpr int WPP = JW / KB;   // warps per column pair
+    extern __shared__ double jsm[];
+    double* sX = jsm;                           // NC x m
+    double* sY = sX + (size_t)NC * a.m;         // NC x n
+    double* snrm = sY + (size_t)NC * a.n;       // [n] norms, for the ordering
+    int* sperm = reinterpret_cast<int*>(snrm + a.n);  // [n] positions -> columns
+    __shared__ double s_part[JW];
+    __shared__ double s_nrm[NC];
+    __shared__ int s_dirty[NC];
+    __shared__ int s_col[NC];
     __shared__ int s_flag;
-    __shared__ double s_red[JW];
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int gw = blockIdx.x, nw = gridDim.x;
-    const int np = a.n + (a.n & 1);
-    const int npairs = np / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = 32 * JW;
+    const int pr = warp / WPP, sub = warp % WPP;  // pair slot of this warp, part of the rows
+    const int nb = (a.n + KB - 1) / KB, nbp = nb + (nb & 1);
+    const int npairs = nbp / 2;
+    unsigned long long rot_count = 0;
     int sweep = 0;
     bool converged = false;
     for (; sweep < a.max_sweeps; ++sweep) {
         if (blockIdx.x == 0 && tid == 0) a.flags[(sweep + 1) % 3] = 0;
-        for (int c = gw; c < a.n; c += nw) {
+        // squared column norms, one warp per column
+        for (int c = blockIdx.x * JW + warp; c < a.n; c += gridDim.x * JW) {
             const double* xc = a.X + (int64_t)c * a.ldx;
             double acc = 0.0;
-            for (int r = tid; r < a.m; r += nthr) {
+            for (int r = lane; r < a.m; r += 32) {
                 const double u = __ldcg(xc + r);
                 acc = fma(u, u, acc);
             }
-            acc = jac_block_sum(acc, s_red);
-            if (tid == 0) {
+            acc = warp_sum(acc);
+            if (lane == 0) {
                 __stcg(a.nrm2 + c, acc);
                 // largest squared norm (positive doubles order like their bit patterns)
                 if (sweep == 0)
@@ -327,60 +546,130 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
             }
         }
         if (!grid_sync(a.bar, &s_flag)) return;
-        // visit columns in decreasing-norm order this sweep (the tournament
-        // pairs positions; perm maps positions to columns)
-        if (blockIdx.x == 0) {
-            for (int c = tid; c < a.n; c += nthr) {
-                const double v = __ldcg(a.nrm2 + c);
-                int rank = 0;
-                for (int d = 0; d < a.n; ++d) {
-                    const double w = __ldcg(a.nrm2 + d);
-                    rank += (w > v) || (w == v && d < c);
-                }
-                __stcg(a.perm + rank, c);
+        // visiting order of this sweep: decreasing norm, ties by index; every
+        // CTA ranks the norms itself into shared memory
+        for (int c = tid; c < a.n; c += nthr) snrm[c] = __ldcg(a.nrm2 + c);
+        __syncthreads();
+        for (int c = tid; c < a.n; c += nthr) {
+            const double v = snrm[c];
+            int rank = 0;
+            for (int d = 0; d < a.n; ++d) {
+                const double w = snrm[d];
+                rank += (w > v) || (w == v && d < c);
             }
+            sperm[rank] = c;
         }
-        if (!grid_sync(a.bar, &s_flag)) return;
+        __syncthreads();
         // pairs of columns that both lie below the truncation cut are dropped
         // after the SVD whatever their rotation, so they are not rotated
         const double cut2 = a.cut * a.cut * __ldcg(a.nrm2 + a.n);
-        for (int t = 0; t < np - 1; ++t) {
-            for (int q = gw; q < npairs; q += nw) {
-                int i, j;
-                if (q == 0) { i = t; j = np - 1; }
-                else { i = (t + q) % (np - 1); j = (t - q + np - 1) % (np - 1); }
-                if (i >= a.n || j >= a.n) continue;
-                i = __ldcg(a.perm + i);
-                j = __ldcg(a.perm + j);
-                double* xi = a.X + (int64_t)i * a.ldx;
-                double* xj = a.X + (int64_t)j * a.ldx;
-                const double al = __ldcg(a.nrm2 + i), be = __ldcg(a.nrm2 + j);
-                double ga = 0.0;
-                for (int r = tid; r < a.m; r += nthr) ga = fma(__ldcg(xi + r), __ldcg(xj + r), ga);
-                ga = jac_block_sum(ga, s_red);
-                if ((al > cut2 || be > cut2) && fabs(ga) > a.tol * sqrt(al) * sqrt(be)) {
-                    double c, s;
-                    jacobi_pair_rot(al, be, ga, c, s);
-                    for (int r = tid; r < a.m; r += nthr) {
-                        const double u = __ldcg(xi + r), v = __ldcg(xj + r);
-                        __stcg(xi + r, c * u - s * v);
-                        __stcg(xj + r, s * u + c * v);
+        for (int t = 0; t < nbp - 1; ++t) {
+            for (int q = blockIdx.x; q < npairs; q += gridDim.x) {
+                int I, J;
+                rr_pair(nbp, t, q, I, J);
+                int cols[NC];
+                unsigned int vmask = 0;  // bit c: staged column c exists
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int pos = c < KB ? I * KB + c : J * KB + c - KB;
+                    cols[c] = pos < a.n ? sperm[pos] : -1;
+                    vmask |= (cols[c] >= 0 ? 1u : 0u) << c;
+                }
+                // stage the columns and their norms: independent loads in flight
+                if (tid < NC) {
+                    const int pos = tid < KB ? I * KB + tid : J * KB + tid - KB;
+                    const int col = pos < a.n ? sperm[pos] : -1;
+                    s_col[tid] = col;
+                    s_nrm[tid] = col >= 0 ? __ldcg(a.nrm2 + col) : 0.0;
+                    s_dirty[tid] = 0;
+                }
+                for (int r = tid; r < a.m; r += nthr) {
+                    double v[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) v[c] = cols[c] >= 0 ? __ldcg(a.X + (int64_t)cols[c] * a.ldx + r) : 0.0;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) sX[c * a.m + r] = v[c];
+                }
+                for (int r = tid; r < a.n; r += nthr) {
+                    double v[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) v[c] = cols[c] >= 0 ? __ldcg(a.Y + (int64_t)cols[c] * a.ldy + r) : 0.0;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) sY[c * a.n + r] = v[c];
+                }
+                __syncthreads();
+                const bool full = (t == 0);
+                const int inner = full ? NC - 1 : KB;
+                for (int s = 0; s < inner; ++s) {
+                    int i, j;
+                    if (full) rr_pair(NC, s, pr, i, j);
+                    else {
+                        i = pr;
+                        j = KB + (pr + s) % KB;
                     }
-                    double* yi = a.Y + (int64_t)i * a.ldy;
-                    double* yj = a.Y + (int64_t)j * a.ldy;
-                    for (int r = tid; r < a.n; r += nthr) {
-                        const double u = __ldcg(yi + r), v = __ldcg(yj + r);
-                        __stcg(yi + r, c * u - s * v);
-                        __stcg(yj + r, s * u + c * v);
+                    const bool valid = ((vmask >> i) & (vmask >> j) & 1u) != 0;
+                    double* xi = sX + (size_t)i * a.m;
+                    double* xj = sX + (size_t)j * a.m;
+                    double g = 0.0;
+                    if (valid)
+                        for (int r = sub * 32 + lane; r < a.m; r += 32 * WPP) g = fma(xi[r], xj[r], g);
+                    g = warp_sum(g);
+                    if (lane == 0) s_part[warp] = g;
+                    __syncthreads();
+                    double ga = 0.0;
+#pragma unroll
+                    for (int w = 0; w < WPP; ++w) ga += s_part[pr * WPP + w];
+                    const double al = s_nrm[i], be = s_nrm[j];
+                    const bool rot = valid && (al > cut2 || be > cut2) &&
+                                     fabs(ga) > a.tol * sqrt(al) * sqrt(be);
+                    double c = 1.0, sn = 0.0;
+                    if (rot) {
+                        jacobi_pair_rot(al, be, ga, c, sn);
+                        for (int r = sub * 32 + lane; r < a.m; r += 32 * WPP) {
+                            const double u = xi[r], v = xj[r];
+                            xi[r] = c * u - sn * v;
+                            xj[r] = sn * u + c * v;
+                        }
+                        double* yi = sY + (size_t)i * a.n;
+                        double* yj = sY + (size_t)j * a.n;
+                        for (int r = sub * 32 + lane; r < a.n; r += 32 * WPP) {
+                            const double u = yi[r], v = yj[r];
+                            yi[r] = c * u - sn * v;
+                            yj[r] = sn * u + c * v;
+                        }
                     }
-                    if (tid == 0) {
+                    // every read of s_part and s_nrm of this inner round is done
+                    __syncthreads();
+                    if (rot && sub == 0 && lane == 0) {
                         // new squared norms: c^2 al - 2cs ga + s^2 be and s^2 al + 2cs ga + c^2 be
-                        const double cs2 = 2.0 * c * s * ga;
-                        __stcg(a.nrm2 + i, fmax(c * c * al - cs2 + s * s * be, 0.0));
-                        __stcg(a.nrm2 + j, fmax(s * s * al + cs2 + c * c * be, 0.0));
-                        atomicExch(a.flags + sweep % 3, 1);
+                        const double cs2 = 2.0 * c * sn * ga;
+                        s_nrm[i] = fmax(c * c * al - cs2 + sn * sn * be, 0.0);
+                        s_nrm[j] = fmax(sn * sn * al + cs2 + c * c * be, 0.0);
+                        s_dirty[i] = 1;
+                        s_dirty[j] = 1;
+                        ++rot_count;
                     }
                 }
+                __syncthreads();
+                bool dirty[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) dirty[c] = s_dirty[c] != 0;
+                for (int r = tid; r < a.m; r += nthr) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        if (dirty[c]) __stcg(a.X + (int64_t)cols[c] * a.ldx + r, sX[c * a.m + r]);
+                }
+                for (int r = tid; r < a.n; r += nthr) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c)
+                        if (dirty[c]) __stcg(a.Y + (int64_t)cols[c] * a.ldy + r, sY[c * a.n + r]);
+                }
+                if (tid < NC && s_dirty[tid]) {
+                    __stcg(a.nrm2 + s_col[tid], s_nrm[tid]);
+                    *(volatile int*)(a.flags + sweep % 3) = 1;
+                }
+                // shared memory is restaged for the next block pair
+                __syncthreads();
             }
             if (!grid_sync(a.bar, &s_flag)) return;
         }
@@ -390,10 +679,16 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
             break;
         }
     }
+    if (rot_count) atomicAdd(a.rotations, rot_count);
     if (blockIdx.x == 0 && tid == 0) {
         *a.sweeps = sweep;
         if (!converged) st_dev_error(a.bar.err, ST_ERR_NOT_CONVERGED);
     }
+}
+
+// Shared memory of the block Jacobi kernel for KB columns per block.
+inline size_t jacobi_smem(int kb, int m, int n) {
+    return sizeof(double) * (2 * (size_t)kb * (m + n) + n) + sizeof(int) * (size_t)n;
 }
 
 // ---------------------------------------------------------------------------
@@ -434,21 +729,23 @@ __global__ void __launch_bounds__(1024) sort_kernel(int m, int n, const double* 
     }
 }
 
-// Ysel[:, q] = Y[:, perm[q]];  Vsel[:, q] = X[:, perm[q]] / sigma_q.
+// Kept singular vectors of the middle matrix Q = (Pi U_z) Sigma (Q1 Y)^T:
+//   Ysel[piv[j], q] = Z[j, perm[q]] / sigma_q        (left, n x rk)
+//   Vsel[:, q] = [Y[:, perm[q]]; 0]                  (right before Q1, m x rk)
 __global__ void gather_kernel(int n, int m, int rk, const int* __restrict__ perm,
-                              const double* __restrict__ sig, const double* __restrict__ Y, int ldy,
-                              const double* __restrict__ X, int ldx, double* Ysel, int ldys,
-                              double* Vsel, int ldvs) {
+                              const int* __restrict__ piv, const double* __restrict__ sig,
+                              const double* __restrict__ Y, int ldy, const double* __restrict__ Z,
+                              int ldz, double* Ysel, int ldys, double* Vsel, int ldvs) {
     const int64_t t1 = (int64_t)n * rk, t2 = (int64_t)m * rk;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < t1 + t2;
          t += (int64_t)gridDim.x * blockDim.x) {
         if (t < t1) {
-            const int i = (int)(t % n), q = (int)(t / n);
-            Ysel[i + (int64_t)q * ldys] = Y[i + (int64_t)perm[q] * ldy];
+            const int j = (int)(t % n), q = (int)(t / n);
+            Ysel[piv[j] + (int64_t)q * ldys] = Z[j + (int64_t)perm[q] * ldz] / sig[q];
         } else {
             const int64_t u = t - t1;
             const int i = (int)(u % m), q = (int)(u / m);
-            Vsel[i + (int64_t)q * ldvs] = X[i + (int64_t)perm[q] * ldx] / sig[q];
+            Vsel[i + (int64_t)q * ldvs] = i < n ? Y[i + (int64_t)perm[q] * ldy] : 0.0;
         }
     }
 }
@@ -571,6 +868,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     m->pod_r = 0;
     m->pod_rows = 0;
     m->sigma.clear();
+    m->pod_sweeps.clear();
+    m->pod_reorth = 0;
 
     // buffers
     ST_TRY(st_grow(m, m->W, sizeof(double) * N * cap));
@@ -588,8 +887,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         gs_blocks = (int)std::min<int64_t>(gs_blocks, std::max<int64_t>(1, N / 64));
     }
     const size_t szPart = std::max((size_t)std::max(gs_blocks, 1) * pdim, (size_t)64 * Nt);
-    const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 2 * szX + (size_t)cap * rmax * 2 +
-                           szPart + pdim + 4 * cap + 32;
+    const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 3 * szX + (size_t)cap * rmax * 2 +
+                           szPart + pdim + 9 * cap + 32;
     ST_TRY(st_grow(m, m->ws_pod, sizeof(double) * doubles + sizeof(int) * (2 * cap + 16)));
     double* W2 = (double*)m->ws_pod.p;
     double* V2 = W2 + szW2;
@@ -601,26 +900,81 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     double* P2 = P1 + szP;
     double* X = P2 + szP;
     double* Y = X + szX;
-    double* Ysel = Y + szX;
+    double* Z = Y + szX;
+    double* Ysel = Z + szX;
     double* Vsel = Ysel + (size_t)cap * rmax;
     double* partial = Vsel + (size_t)cap * rmax;
     double* hbuf = partial + szPart;
-    double* d_sig = hbuf + pdim;         // [cap] current sigma (device copy)
+    double* q_beta = hbuf + pdim;        // [cap] R diagonal of the pivoted QR
+    double* q_tau = q_beta + cap;        // [cap] Householder coefficients
+    double* q_scale = q_tau + cap;       // [cap] 1 / (x_k - beta_k)
+    double* q_nrm = q_scale + cap;       // [2 cap] trailing squared norms (double buffered)
+    double* d_sig = q_nrm + 2 * cap;     // [cap] current sigma (device copy)
     double* d_sig_sorted = d_sig + cap;  // [cap]
     double* d_sig_tmp = d_sig_sorted + cap;
     double* d_scalar = d_sig_tmp + cap + 8;  // [16]: tau, dot (d_sig_tmp[cap] is the Jacobi norm max)
     int* d_int = (int*)(d_scalar + 16);  // [16]: k, r_new, sweeps, flags[3]
     int* d_perm = d_int + 16;            // [cap]
+    int* d_piv = d_perm + cap;           // [cap] column pivots of the QR
+    unsigned long long* d_rot = reinterpret_cast<unsigned long long*>(d_scalar + 4);
     double* W = (double*)m->W.p;
     double* V = (double*)m->V.p;
 
-    int jac_blocks_max = 0;
-    {
-        int per_sm = 0;
-        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, 32 * JW, 0));
-        jac_blocks_max = std::max(1, std::min(per_sm, 2)) * m->num_sms;
-    }
     const GridBarrier bar{m->d_bar, m->d_bar + 1, m->d_bar + 2, m->d_err, m->opt.spin_limit};
+    // pivoted Householder QR of the transposed middle matrix
+    auto run_qrp = [&](int mrows, int ncols) -> st_status {
+        const size_t smem = sizeof(double) * mrows;
+        if (smem > 48 * 1024)
+            ST_CUDA_TRY(cudaFuncSetAttribute(qrp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrp_kernel, QT, smem));
+        if (per_sm < 1) return st_fail(ST_ERR_CUDA, "st_rom_build_basis: QR kernel does not fit on an SM");
+        const int qb = std::max(1, std::min({per_sm * m->num_sms, m->num_sms, (ncols + 1) / 2}));
+        ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
+        QrpArgs qa{mrows, ncols, X, cap, q_beta, q_tau, q_scale, d_piv, q_nrm, bar};
+        void* args[] = {&qa};
+        ST_PROF(m, "qrp_kernel");
+        ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)qrp_kernel, dim3(qb), dim3(QT), args, smem, st));
+        st_count_launch();
+        double fl = 0.0;
+        for (int kk = 0; kk < ncols; ++kk) fl += 2.0 * (mrows - kk) + 6.0 * (ncols - kk - 1) * (mrows - kk);
+        st_prof_flops(m, "qrp_kernel", fl + 2.0 * mrows * ncols);
+        return ST_OK;
+    };
+    // middle-matrix SVD: KB columns per Jacobi block, fewer where the staged
+    // columns would not fit in shared memory
+    auto run_jacobi = [&](int mrows, int ncols) -> st_status {
+        int kb = ST_JACOBI_KB;
+        while (kb > 1 && jacobi_smem(kb, mrows, ncols) > kJacobiSmemMax) kb /= 2;
+        const size_t smem = jacobi_smem(kb, mrows, ncols);
+        if (smem > kJacobiSmemMax)
+            return st_fail(ST_ERR_ARG, "st_rom_build_basis: r_max + Nt too large for the middle-matrix SVD");
+        const void* fn = kb == 4 ? (const void*)jacobi_kernel<4>
+                       : kb == 2 ? (const void*)jacobi_kernel<2> : (const void*)jacobi_kernel<1>;
+        ST_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * JW, smem));
+        if (per_sm < 1) return st_fail(ST_ERR_CUDA, "st_rom_build_basis: Jacobi kernel does not fit on an SM");
+        const int nb = (ncols + kb - 1) / kb;
+        const int npairs = (nb + (nb & 1)) / 2;
+        const int jb = std::max(1, std::min(per_sm * m->num_sms, npairs));
+        ST_CUDA_TRY(cudaMemsetAsync(d_int + 3, 0, sizeof(int) * 3, st));
+        ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
+        // the largest squared column norm is accumulated with atomicMax from zero
+        ST_CUDA_TRY(cudaMemsetAsync(d_sig_tmp + ncols, 0, sizeof(double), st));
+        ST_CUDA_TRY(cudaMemsetAsync(d_rot, 0, sizeof(unsigned long long), st));
+        // Z = R^T: stop when every pair of columns is orthogonal to
+        // sqrt(m) * eps relative (the left singular vectors of the middle
+        // matrix are these columns, normalised)
+        JacArgs ja{mrows, ncols, Z, cap, Y, cap, m->opt.jacobi_sweeps,
+                   std::sqrt((double)mrows) * 2.220446049250313e-16, d_int + 3, d_int + 2, d_sig_tmp,
+                   0.1 * m->opt.eps_sv, d_rot, bar};
+        void* args[] = {&ja};
+        ST_PROF(m, "jacobi_kernel");
+        ST_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(jb), dim3(32 * JW), args, smem, st));
+        st_count_launch();
+        return ST_OK;
+    };
     int r = 0;
     int64_t rows = 0;
     std::vector<double> h_sig;
@@ -629,6 +983,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
         Gs2Args g{N, mcols, Ein, Jout, Pout, d_int, tau, partial, hbuf, bar};
         void* args[] = {&g};
+        ST_PROF(m, "gs2_kernel");
         ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT), args,
                                                 sizeof(double) * 2 * pdim, st));
         st_count_launch();
@@ -646,6 +1001,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         const double* Up = snapshots + (size_t)p * Nt * N;
         {
             const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(64, N / 2048));
+            ST_PROF(m, "colnorm_kernels");
             colnorm_part_kernel<<<dim3(Nt, chunks), NT, 0, st>>>(N, Up, chunks, partial);
             ST_TRY(st_check_launch("colnorm_part"));
             colnorm_max_kernel<<<1, NT, 0, st>>>(Nt, chunks, partial, m->opt.eps_svd, d_scalar);
@@ -670,8 +1026,11 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
                 ST_TRY(st_dgemm(m, false, false, N, k1, r, -1.0, W, N, L2, rmax, 1.0, E, N));
                 ST_TRY(st_dgemm(m, true, false, k1, k1, N, 1.0, E, N, E, N, 0.0, Y, k1));
                 ST_CUDA_TRY(cudaMemsetAsync(d_int + 6, 0, sizeof(int), st));
-                chol_inv_kernel<<<1, NT, 0, st>>>(k1, Y, P2, k1, X, d_int + 6);
-                ST_TRY(st_check_launch("chol_inv"));
+                {
+                    ST_PROF(m, "chol_inv_kernel");
+                    chol_inv_kernel<<<1, NT, 0, st>>>(k1, Y, P2, k1, X, d_int + 6);
+                    ST_TRY(st_check_launch("chol_inv"));
+                }
                 int chol_fail = 0;
                 ST_CUDA_TRY(cudaMemcpyAsync(&chol_fail, d_int + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
                 ST_CUDA_TRY(cudaStreamSynchronize(st));
@@ -694,31 +1053,33 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             rows += Nt;
             continue;
         }
+        // middle matrix, transposed: X = Q^T (mrows x ncols); pivoted QR
+        // X Pi = Q1 R, then one-sided Jacobi on Z = R^T with rotations
+        // accumulated in Y:  Q = (Pi U_z) Sigma (Q1 Y)^T
         build_qt_kernel<<<grid_for(m, (int64_t)mrows * ncols), 256, 0, st>>>(r, k, Nt, d_sig, L, rmax, P, Nt, X, cap);
         ST_TRY(st_check_launch("build_qt"));
-        eye_kernel<<<grid_for(m, (int64_t)ncols * ncols), 256, 0, st>>>(ncols, Y, cap);
-        ST_TRY(st_check_launch("eye"));
-        ST_CUDA_TRY(cudaMemsetAsync(d_int + 3, 0, sizeof(int) * 3, st));
-        ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
-        // the largest squared column norm is accumulated with atomicMax from zero
-        ST_CUDA_TRY(cudaMemsetAsync(d_sig_tmp + ncols, 0, sizeof(double), st));
+        ST_TRY(run_qrp(mrows, ncols));
+        build_rt_kernel<<<grid_for(m, (int64_t)ncols * ncols), 256, 0, st>>>(ncols, X, cap, d_piv, q_beta, Z, cap, Y, cap);
+        ST_TRY(st_check_launch("build_rt"));
+        ST_TRY(run_jacobi(ncols, ncols));
         {
-            const int npairs = (ncols + 1) / 2;
-            int jb = std::max(1, std::min(jac_blocks_max, npairs));
-            // stop when every pair is orthogonal to m * eps relative
-            JacArgs ja{mrows, ncols, X, cap, Y, cap, m->opt.jacobi_sweeps,
-                       (double)mrows * 2.220446049250313e-16, d_int + 3, d_int + 2, d_sig_tmp,
-                       0.1 * m->opt.eps_sv, d_perm, bar};
-            void* args[] = {&ja};
-            ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(jb), dim3(32 * JW), args, 0, st));
-        st_count_launch();
+            ST_PROF(m, "sort_kernel");
+            sort_kernel<<<1, 1024, 0, st>>>(ncols, ncols, Z, cap, m->opt.eps_sv, rmax, d_sig_sorted,
+                                            d_perm, d_int + 1, d_sig_tmp, m->d_err);
+            ST_TRY(st_check_launch("sort"));
         }
-        sort_kernel<<<1, 1024, 0, st>>>(mrows, ncols, X, cap, m->opt.eps_sv, rmax, d_sig_sorted,
-                                        d_perm, d_int + 1, d_sig_tmp, m->d_err);
-        ST_TRY(st_check_launch("sort"));
-        int rnew = 0;
-        ST_CUDA_TRY(cudaMemcpyAsync(&rnew, d_int + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int rs[2] = {0, 0};  // r_new, sweeps
+        unsigned long long nrot = 0;
+        ST_CUDA_TRY(cudaMemcpyAsync(rs, d_int + 1, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+        ST_CUDA_TRY(cudaMemcpyAsync(&nrot, d_rot, sizeof(nrot), cudaMemcpyDeviceToHost, st));
         ST_CUDA_TRY(cudaStreamSynchronize(st));
+        const int rnew = rs[0];
+        m->pod_sweeps.push_back(rs[1]);
+        // algorithmic work: per sweep the column norms (2 m n) and a dot
+        // product per pair (2 m); per rotation 6 (m + n)
+        st_prof_flops(m, "jacobi_kernel",
+                      rs[1] * (2.0 * ncols * ncols + (double)ncols * (ncols - 1) * ncols) +
+                          12.0 * (double)nrot * ncols);
         {
             int32_t herr = 0;
             ST_CUDA_TRY(cudaMemcpy(&herr, m->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -730,8 +1091,22 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             continue;
         }
         gather_kernel<<<grid_for(m, (int64_t)(ncols + mrows) * rnew), 256, 0, st>>>(
-            ncols, mrows, rnew, d_perm, d_sig_sorted, Y, cap, X, cap, Ysel, cap, Vsel, cap);
+            ncols, mrows, rnew, d_perm, d_piv, d_sig_sorted, Y, cap, Z, cap, Ysel, cap, Vsel, cap);
         ST_TRY(st_check_launch("gather"));
+        {
+            // Vsel <- Q1 Vsel, the reflectors of the QR applied in reverse order
+            ST_PROF(m, "apply_q_kernel");
+            const int wpb = 4;
+            const size_t smem = sizeof(double) * mrows;
+            if (smem > 48 * 1024)
+                ST_CUDA_TRY(cudaFuncSetAttribute(apply_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            apply_q_kernel<<<(rnew + wpb - 1) / wpb, 32 * wpb, smem, st>>>(mrows, ncols, rnew, X, cap, d_piv, q_tau,
+                                                                          q_scale, Vsel, cap);
+            ST_TRY(st_check_launch("apply_q"));
+            double fl = 0.0;
+            for (int kk = 0; kk < ncols; ++kk) fl += 4.0 * (mrows - kk);
+            st_prof_flops(m, "apply_q_kernel", fl * rnew);
+        }
         // W2 = [W J] Ysel
         ST_TRY(st_dgemm(m, false, false, N, rnew, ncols, 1.0, W, N, Ysel, cap, 0.0, W2, N));
         // V2 = blkdiag(V, I) Vsel
@@ -753,10 +1128,12 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             ST_CUDA_TRY(cudaMemcpyAsync(&dotv, d_scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
             ST_CUDA_TRY(cudaStreamSynchronize(st));
             if (std::fabs(dotv) > std::min(m->opt.eps_svd, 2.220446049250313e-16 * (double)N)) {
+                ++m->pod_reorth;
                 ST_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)r * r, st));
                 ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
                 Gs2Args g{N, r, W, W2, P, d_int, nullptr, partial, hbuf, bar};
                 void* args[] = {&g};
+                ST_PROF(m, "gs2_kernel");
                 ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT),
                                                         args, sizeof(double) * 2 * pdim, st));
         st_count_launch();
@@ -784,6 +1161,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         if (smem > 220 * 1024) return st_fail(ST_ERR_ARG, "st_rom_build_basis: Nt * n_mu too large for the temporal SVD");
         if (smem > 48 * 1024)
             ST_CUDA_TRY(cudaFuncSetAttribute(temporal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ST_PROF(m, "temporal_kernel");
         temporal_kernel<<<ns, 512, smem, st>>>(Nt, n_mu, ns, nt, V, ldv, m->d_T, m->opt.jacobi_sweeps,
                                                std::sqrt((double)Nt) * 2.220446049250313e-16, m->d_err);
         ST_TRY(st_check_launch("temporal"));

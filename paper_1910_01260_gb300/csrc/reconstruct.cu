@@ -56,8 +56,11 @@ extern "C" st_status st_rom_reconstruct(st_model* m, int32_t n_mu, const double*
     double* C = (double*)m->ws_misc.p;
     double* Chat = C + szC;
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)szC + 255) / 256, 8 * m->num_sms));
-    temporal_contract_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, Nt, uhat, ns_nt, m->d_T, C);
-    ST_TRY(st_check_launch("temporal_contract"));
+    {
+        ST_PROF(m, "temporal_contract_kernel");
+        temporal_contract_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, Nt, uhat, ns_nt, m->d_T, C);
+        ST_TRY(st_check_launch("temporal_contract"));
+    }
     const int64_t sCp = (int64_t)ns * Nt;
     for (int p0 = 0; p0 < n_mu; p0 += 65535) {
         const int nb = std::min(65535, n_mu - p0);

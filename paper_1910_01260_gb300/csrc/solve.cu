@@ -513,12 +513,16 @@ extern "C" st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta
     int* hist = order + n_mu;
     ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n_mu + 255) / 256, 4 * m->num_sms));
-    size_hist_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, ns_nt, npv, hist);
-    size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
-    size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
-    ST_TRY(st_check_launch("solve order"));
+    {
+        ST_PROF(m, "size_sort_kernels");
+        size_hist_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, ns_nt, npv, hist);
+        size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
+        size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
+        ST_TRY(st_check_launch("solve order"));
+    }
     ST_CUDA_TRY(cudaMemsetAsync(m->d_bar + 3, 0, sizeof(unsigned int), st));
     SolveArgs g = solve_args(m, n_mu, theta, ns_nt, uhat, rel_res, status, order, m->d_bar + 3, ws, nb);
+    ST_PROF(m, f32 ? "solve_kernel<float>" : "solve_kernel<double>");
     if (f32) solve_kernel<float><<<blocks, NT, smem, st>>>(g);
     else solve_kernel<double><<<blocks, NT, smem, st>>>(g);
     return st_check_launch("solve");
@@ -540,6 +544,7 @@ st_status st_internal_solve_list(st_model* m, int n_list, const int* list, const
     ST_CUDA_TRY(cudaMemsetAsync(m->d_bar + 3, 0, sizeof(unsigned int), st));
     SolveArgs g = solve_args(m, n_list, theta, nullptr, uhat, rel_res, status, list, m->d_bar + 3,
                              (double*)m->ws_solve.p, nb);
+    ST_PROF(m, f32 ? "solve_kernel<float>" : "solve_kernel<double>");
     if (f32) solve_kernel<float><<<blocks, NT, smem, st>>>(g);
     else solve_kernel<double><<<blocks, NT, smem, st>>>(g);
     return st_check_launch("solve_list");
@@ -634,11 +639,15 @@ extern "C" st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double
     ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
     ST_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st));
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n_mu + 255) / 256, 4 * m->num_sms));
-    size_hist_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, ns_nt, npv, hist);
-    size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
-    size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
-    ST_TRY(st_check_launch("solve_static order"));
+    {
+        ST_PROF(m, "size_sort_kernels");
+        size_hist_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, ns_nt, npv, hist);
+        size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
+        size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
+        ST_TRY(st_check_launch("solve_static order"));
+    }
     SolveArgs g = solve_args(m, n_mu, theta, ns_nt, uhat, rel_res, status, order, queue, ws, nb);
+    ST_PROF(m, f32 ? "solve_kernel<float>" : "solve_kernel<double>");
     if (f32) solve_kernel<float><<<blocks, NT, smem, st>>>(g);
     else solve_kernel<double><<<blocks, NT, smem, st>>>(g);
     return st_check_launch("solve_static");

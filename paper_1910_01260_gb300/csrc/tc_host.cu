@@ -47,6 +47,8 @@ st_status launch(st_model* m, int M, int N, const CUtensorMap& ta, const CUtenso
     const size_t smem = tc::smem_bytes(BN);
     ST_CUDA_TRY(cudaFuncSetAttribute(tc::gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((M + tc::kBM - 1) / tc::kBM, (N + BN - 1) / BN);
+    ST_PROF(m, "tc_gemm_kernel");
+    st_prof_flops(m, "tc_gemm_kernel", 2.0 * (double)M * (double)N * (double)g.K);
     tc::gemm_kernel<BN><<<grid, tc::kThreads, smem, m->stream>>>(ta, tb, g);
     return st_check_launch("tc_gemm");
 }

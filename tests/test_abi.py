@@ -106,4 +106,7 @@ def test_null_handle_arguments(st):
     assert st.lib.st_sync(None) == st.ST_ERR_ARG
     assert st.lib.st_rom_solve(None, 1, None, None, None, None, None) == st.ST_ERR_ARG
     assert st.lib.st_rom_assemble(None, None, 0, None, None, None) == st.ST_ERR_ARG
+    assert st.lib.st_profile_enable(None, 1) == st.ST_ERR_ARG
+    assert st.lib.st_profile_read(None, 0, None, None, None, None, None) == st.ST_ERR_ARG
+    assert st.lib.st_pod_get_stats(None, None, None, 0, None) == st.ST_ERR_ARG
     st.lib.st_model_destroy(None)

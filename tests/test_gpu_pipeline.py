@@ -49,3 +49,33 @@ def test_c1_end_to_end():
         assert strom.rel_error(fom_test[k], U[k].T) < 1e-2
     assert res.max().item() < 1e-12
     m.close()
+
+
+def test_profile_and_pod_stats():
+    """Per-kernel event timing covers the launches of every stage, GEMM and
+    Jacobi flops are counted, and the POD diagnostics match the update count."""
+    torch = __import__("torch")
+    p = problem_for("c1")
+    m = make_model(p, r_max=200)
+    B = dev_B(p)
+    nmu = len(p.train_mu)
+    snaps = torch.empty((nmu, p.Nt, p.N), dtype=torch.float64, device="cuda:0")
+    m.st_profile_enable(True)
+    m.st_fom_march(p.theta(p.train_mu), p.dt, None, B, p.F, snaps)
+    m.st_rom_build_basis(nmu, p.Nt, snaps, p.ns, p.nt)
+    m.st_rom_assemble(p.dt, B, p.F, None)
+    uhat = torch.zeros((3, p.ns * p.nt), dtype=torch.float64, device="cuda:0")
+    m.st_rom_solve(3, dev_tensor(p.theta(p.test_mu[:3])), None, uhat)
+    prof = m.st_profile_read()
+    for name in ("fom_march_kernel", "jacobi_kernel", "dgemm_kernel", "solve_kernel<double>", "gs2_kernel"):
+        assert name in prof and prof[name][0] > 0.0 and prof[name][1] >= 1, name
+    assert prof["dgemm_kernel"][2] > 0 and prof["jacobi_kernel"][2] > 0
+    times = [v[0] for v in prof.values()]
+    assert times == sorted(times, reverse=True)
+    sweeps, reorth = m.st_pod_get_stats()
+    assert len(sweeps) == nmu and all(1 <= s <= 40 for s in sweeps) and reorth >= 0
+    assert prof["jacobi_kernel"][1] == nmu
+    m.st_profile_enable(False)
+    m.st_rom_solve(3, dev_tensor(p.theta(p.test_mu[:3])), None, uhat)
+    assert m.st_profile_read() == {}
+    m.close()

@@ -83,3 +83,25 @@ def test_pod_2d_several_blocks():
                      ns=10, nt=4)
     blocks = oracle_fom(p, p.train_mu)
     _compare(p, blocks, 120, p.ns, p.nt)
+
+
+def test_fom_and_pod_are_deterministic():
+    """The FOM march and the POD use fixed-order reductions only: two runs on
+    the same inputs agree bit for bit (2-D model, several blocks)."""
+    torch = __import__("torch")
+    p = make_problem(dim=2, M=16, quad="s4", Nt=30, train=(2, 2), ns=6, nt=2)
+    m = make_model(p, r_max=64)
+    B = dev_tensor(p.B.T.copy())
+    nmu = len(p.train_mu)
+    runs = []
+    for _ in range(2):
+        snaps = torch.empty((nmu, p.Nt, p.N), dtype=torch.float64, device="cuda:0")
+        m.st_fom_march(p.theta(p.train_mu), p.dt, None, B, p.F, snaps)
+        sig, r = m.st_rom_build_basis(nmu, p.Nt, snaps, p.ns, p.nt)
+        W = torch.zeros((r, p.N), dtype=torch.float64, device="cuda:0")
+        m.st_pod_get_state(W)
+        runs.append((snaps.cpu().numpy(), sig.copy(), W.cpu().numpy(), m.st_pod_get_stats()[0]))
+    (s0, g0, w0, k0), (s1, g1, w1, k1) = runs
+    assert np.array_equal(s0, s1)
+    assert np.array_equal(g0, g1) and np.array_equal(w0, w1) and k0 == k1
+    m.close()
