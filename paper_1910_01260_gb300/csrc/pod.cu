@@ -487,7 +487,7 @@ __device__ __forceinline__ void jacobi_pair_rot(double alpha, double beta, doubl
     s = c * t;
 }
 
-constexpr int JW = 4;  // warps per Jacobi CTA
+constexpr int JW = 8;  // warps per Jacobi CTA
 #ifndef ST_JACOBI_KB
 #define ST_JACOBI_KB 2
 #endif
@@ -610,10 +610,16 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
                     const bool valid = ((vmask >> i) & (vmask >> j) & 1u) != 0;
                     double* xi = sX + (size_t)i * a.m;
                     double* xj = sX + (size_t)j * a.m;
-                    double g = 0.0;
-                    if (valid)
-                        for (int r = sub * 32 + lane; r < a.m; r += 32 * WPP) g = fma(xi[r], xj[r], g);
-                    g = warp_sum(g);
+                    double g = 0.0, g2 = 0.0;
+                    if (valid) {
+                        int r = sub * 32 + lane;
+                        for (; r + 32 * WPP < a.m; r += 64 * WPP) {
+                            g = fma(xi[r], xj[r], g);
+                            g2 = fma(xi[r + 32 * WPP], xj[r + 32 * WPP], g2);
+                        }
+                        if (r < a.m) g = fma(xi[r], xj[r], g);
+                    }
+                    g = warp_sum(g + g2);
                     if (lane == 0) s_part[warp] = g;
                     __syncthreads();
                     double ga = 0.0;
