@@ -551,7 +551,8 @@ def run_case(case: str) -> None:
     fom: FOM march of the 16 training parameters, 10 steps (one launch);
     pod: full-size snapshots, then the incremental POD;
     solve: seeded (40,12) bases, the 4096-parameter batch in FP64 and FP32-LU;
-    mlp: surrogate forward (tcgen05 GEMMs) on 65,536 parameters."""
+    mlp: surrogate forward (tcgen05 GEMMs) on 65,536 parameters;
+    fomfull: the full 200-step march of the 16 training parameters, timed."""
     import torch
 
     import paper_1910_01260_gb300 as st
@@ -562,10 +563,20 @@ def run_case(case: str) -> None:
     m = st.Model(prob.rowptr, prob.col, prob.vals, st.options(eps_svd=EPS_SVD), stream=stream.cuda_stream)
     B = torch.tensor(prob.B.T.copy(), device=dev)
     n_train = len(prob.train_mu)
-    if case in ("fom", "pod"):
+    if case in ("fom", "fomfull", "pod"):
         Nt = 10 if case == "fom" else prob.Nt
         snaps = torch.empty((n_train, Nt, prob.N), dtype=torch.float64, device=dev)
         m.st_fom_march(prob.theta(prob.train_mu), prob.dt[:Nt], None, B, prob.F[:Nt], snaps)
+        if case == "fomfull":
+            iters = torch.zeros((Nt, n_train), dtype=torch.int32, device=dev)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            m.st_fom_march(prob.theta(prob.train_mu), prob.dt, None, B, prob.F, snaps, iters)
+            t1.record(stream)
+            m.st_sync()
+            print(json.dumps({"fom_ms": t0.elapsed_time(t1), "iters_mean": float(iters.float().mean()),
+                              "snap_checksum": float(snaps.abs().sum())}))
         if case == "pod":
             m.st_rom_build_basis(n_train, Nt, snaps, prob.ns, prob.nt)
             m.st_sync()
@@ -630,7 +641,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=200)
-    ap.add_argument("--case", default=None, help="run one small profiling workload: fom, pod, solve, mlp")
+    ap.add_argument("--case", default=None, help="run one profiling workload: fom, fomfull, pod, solve, mlp")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)

@@ -5,10 +5,15 @@
 // Design (GB300): one cooperative persistent kernel runs the whole march
 // (all Nt steps, every BiCGSTAB iteration) with all iteration control on the
 // device -- no host round trip per iteration or step.  The samples share
-// the sparsity pattern, so the matrix values of A(mu_p) are stored
-// interleaved per entry ([entry][sample], samples fastest) and every vector
-// is [row][sample]: one gathered column index serves all samples and each
-// thread moves two samples per 128-bit load.  Dot products reduce
+// the sparsity pattern.  The operator is read in its term-split form: an
+// entry where only term q of A(mu) = sum_q theta_q A_q is nonzero keeps one
+// value for all samples and its row sum is scaled by theta_q once; only the
+// entries where several terms overlap (the diagonal, for transport) carry
+// per-sample values, interleaved per entry ([entry][sample]).  The operator
+// thus stays a few MB and the whole march (operator + 7 Krylov vectors)
+// stays resident in L2.  Every vector is [row][sample]: one gathered column
+// index serves all samples and each thread moves two samples per 128-bit
+// load.  Dot products reduce
 // warp -> block -> per-block partials -> fixed-order sums done redundantly
 // by every block after a bounded grid barrier, so all blocks take the same
 // branch decisions and results are deterministic.
@@ -22,23 +27,32 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NSLOT = 2;
+#ifndef ST_FOM_BLOCKS_PER_SM
+#define ST_FOM_BLOCKS_PER_SM 2
+#endif
 
 // per-sample control states
 enum : int { S_ACTIVE = 0, S_CONV = 1, S_FAILED = 2, S_PAD = 3, S_CONV_S = 4, S_ZERO = 5 };
 
 struct FomArgs {
     int64_t N;
-    const int64_t* slice_ptr;
-    const int32_t* slice_w;
-    const int32_t* col;
-    const double* amu;  // [ell * LD]
+    int Q;
+    const double* theta;      // [n_mu x Q] affine coefficients of the group
+    const int64_t* mx_ptr;    // mixed entries (several nonzero terms)
+    const int32_t* mx_w;
+    const int32_t* mx_col;
+    const double* amu;        // [mx_size * LD] their per-sample values
+    const int64_t* tq_ptr;    // entries of a single term q
+    const int32_t* tq_w;
+    const int32_t* tq_col;
+    const double* tq_val;
     int Nt;
     const double* dt;  // [Nt]
     int n_in;
     const double* B;  // [N x n_in]
     const double* F;  // [Nt x n_in]
     double *x, *r, *rh, *p, *v, *s, *t;  // [N * LD]
-    double* partial;                     // [grid * NSLOT * LD]
+    double* partial;                     // [2 x grid * NSLOT * LD]
     double* snap;
     int n_mu;
     int32_t* iters;
@@ -85,25 +99,50 @@ __device__ __forceinline__ void st_vec(double* p, const double (&o)[VEC]) {
     }
 }
 
-// acc = (A(mu) X)[row] for this thread's samples.
+// acc = (A(mu) X)[row] for this thread's samples, A(mu) = sum_q theta_q A_q:
+// the mixed entries carry per-sample values; the entries of a single term q
+// share one value and their row sum is scaled by theta_q(mu) once, so the
+// operator read per product is one value per entry, not one per sample.
 template <int LD>
 __device__ __forceinline__ void spmv_A(const FomArgs& a, int64_t row, int p0, const double* X,
-                                       double (&acc)[Cfg<LD>::VEC]) {
+                                       const double (*s_theta)[LD], double (&acc)[Cfg<LD>::VEC]) {
     constexpr int VEC = Cfg<LD>::VEC;
     const int64_t sl = row / kSlice;
     const int lane = (int)(row % kSlice);
-    const int w = __ldg(a.slice_w + sl);
-    const int64_t base = __ldg(a.slice_ptr + sl) + lane;
 #pragma unroll
     for (int u = 0; u < VEC; ++u) acc[u] = 0.0;
-    for (int k = 0; k < w; ++k) {
-        const int64_t e = base + (int64_t)k * kSlice;
-        const int c = __ldg(a.col + e);
-        double av[VEC], xv[VEC];
-        ld_vec_ro<VEC>(a.amu + e * LD + p0, av);
-        ld_vec<VEC>(X + (int64_t)c * LD + p0, xv);
+    {
+        const int w = __ldg(a.mx_w + sl);
+        const int64_t base = __ldg(a.mx_ptr + sl) + lane;
+        for (int k = 0; k < w; ++k) {
+            const int64_t e = base + (int64_t)k * kSlice;
+            const int c = __ldg(a.mx_col + e);
+            double av[VEC], xv[VEC];
+            ld_vec_ro<VEC>(a.amu + e * LD + p0, av);
+            ld_vec<VEC>(X + (int64_t)c * LD + p0, xv);
 #pragma unroll
-        for (int u = 0; u < VEC; ++u) acc[u] = fma(av[u], xv[u], acc[u]);
+            for (int u = 0; u < VEC; ++u) acc[u] = fma(av[u], xv[u], acc[u]);
+        }
+    }
+    for (int q = 0; q < a.Q; ++q) {
+        const int64_t i = sl * a.Q + q;
+        const int w = __ldg(a.tq_w + i);
+        if (w == 0) continue;
+        const int64_t base = __ldg(a.tq_ptr + i) + lane;
+        double sq[VEC];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) sq[u] = 0.0;
+        for (int k = 0; k < w; ++k) {
+            const int64_t e = base + (int64_t)k * kSlice;
+            const int c = __ldg(a.tq_col + e);
+            const double v = __ldg(a.tq_val + e);
+            double xv[VEC];
+            ld_vec<VEC>(X + (int64_t)c * LD + p0, xv);
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) sq[u] = fma(v, xv[u], sq[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[u] = fma(s_theta[q][p0 + u], sq[u], acc[u]);
     }
 }
 
@@ -150,7 +189,7 @@ __device__ __forceinline__ void grid_reduce(const double* partial, double (*s_re
 }
 
 template <int LD>
-__global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
+__global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(FomArgs a) {
     using C = Cfg<LD>;
     constexpr int VEC = C::VEC, LPR = C::LPR, RPB = C::RPB, NW = C::NW;
     __shared__ double s_warp[NW][NSLOT][LD];
@@ -158,6 +197,7 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
     __shared__ double s_rho[LD], s_rho_old[LD], s_alpha[LD], s_omega[LD], s_beta[LD], s_bnorm[LD];
     __shared__ int s_state[LD], s_it[LD], s_code[LD];
     __shared__ int s_any, s_flag;
+    __shared__ double s_theta[16][LD];
 
     const int lr = threadIdx.x % LPR;
     const int rb = threadIdx.x / LPR;
@@ -169,7 +209,18 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
         s_state[threadIdx.x] = threadIdx.x < a.n_mu ? S_ACTIVE : S_PAD;
         s_code[threadIdx.x] = ST_OK;
     }
+    for (int i = threadIdx.x; i < a.Q * LD; i += NT) {
+        const int q = i / LD, p = i % LD;
+        s_theta[q][p] = p < a.n_mu ? a.theta[(int64_t)p * a.Q + q] : 0.0;
+    }
     __syncthreads();
+    // The per-block partial sums alternate between two buffers: a block may
+    // write the next reduction's partials while a slower block is still
+    // summing the previous ones; a buffer is rewritten only two barriers
+    // after it was read.
+    int red = 0;
+    const size_t part_stride = (size_t)gridDim.x * NSLOT * LD;
+#define PART (a.partial + (size_t)(red & 1) * part_stride)
 
 #define ROWS_BEGIN                                                                    \
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {                   \
@@ -189,7 +240,7 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
                 double bf = 0.0;
                 for (int s = 0; s < a.n_in; ++s) bf = fma(__ldg(a.B + row + (int64_t)s * N), __ldg(a.F + (int64_t)k * a.n_in + s), bf);
                 double Au[VEC], xv[VEC];
-                spmv_A<LD>(a, row, p0, a.x, Au);
+                spmv_A<LD>(a, row, p0, a.x, s_theta, Au);
                 ld_vec<VEC>(a.x + vi, xv);
                 double rr[VEC], zero[VEC];
 #pragma unroll
@@ -208,10 +259,11 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
                 st_vec<VEC>(a.p + vi, zero);
                 st_vec<VEC>(a.v + vi, zero);
             ROWS_END
-            block_partial<LD, 2>(c, a.partial, s_warp);
+            block_partial<LD, 2>(c, PART, s_warp);
         }
         if (!grid_sync(a.bar, &s_flag)) return;
-        grid_reduce<LD, 2>(a.partial, s_red);
+        grid_reduce<LD, 2>(PART, s_red);
+        ++red;
         if (threadIdx.x < LD) {
             const int p = threadIdx.x;
             s_it[p] = 0;
@@ -278,7 +330,7 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
                 for (int u = 0; u < VEC; ++u) c[0][u] = 0.0;
                 ROWS_BEGIN
                     double Ap[VEC], pv[VEC], rhv[VEC], vv[VEC];
-                    spmv_A<LD>(a, row, p0, a.p, Ap);
+                    spmv_A<LD>(a, row, p0, a.p, s_theta, Ap);
                     ld_vec<VEC>(a.p + vi, pv);
                     ld_vec<VEC>(a.rh + vi, rhv);
                     ld_vec<VEC>(a.v + vi, vv);
@@ -290,10 +342,11 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
                         }
                     st_vec<VEC>(a.v + vi, vv);
                 ROWS_END
-                block_partial<LD, 1>(c, a.partial, s_warp);
+                block_partial<LD, 1>(c, PART, s_warp);
             }
             if (!grid_sync(a.bar, &s_flag)) return;
-            grid_reduce<LD, 1>(a.partial, s_red);
+            grid_reduce<LD, 1>(PART, s_red);
+            ++red;
             if (threadIdx.x < LD) {
                 const int p = threadIdx.x;
                 if (s_state[p] == S_ACTIVE) {
@@ -328,10 +381,11 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
                         }
                     st_vec<VEC>(a.s + vi, sv);
                 ROWS_END
-                block_partial<LD, 1>(c, a.partial, s_warp);
+                block_partial<LD, 1>(c, PART, s_warp);
             }
             if (!grid_sync(a.bar, &s_flag)) return;
-            grid_reduce<LD, 1>(a.partial, s_red);
+            grid_reduce<LD, 1>(PART, s_red);
+            ++red;
             if (threadIdx.x < LD) {
                 const int p = threadIdx.x;
                 if (s_state[p] == S_ACTIVE) {
@@ -352,7 +406,7 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
                 for (int u = 0; u < VEC; ++u) c[0][u] = c[1][u] = 0.0;
                 ROWS_BEGIN
                     double As[VEC], sv[VEC], tv[VEC], xv[VEC], pv[VEC];
-                    spmv_A<LD>(a, row, p0, a.s, As);
+                    spmv_A<LD>(a, row, p0, a.s, s_theta, As);
                     ld_vec<VEC>(a.s + vi, sv);
                     ld_vec<VEC>(a.t + vi, tv);
                     ld_vec<VEC>(a.x + vi, xv);
@@ -371,10 +425,11 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
                     st_vec<VEC>(a.t + vi, tv);
                     st_vec<VEC>(a.x + vi, xv);
                 ROWS_END
-                block_partial<LD, 2>(c, a.partial, s_warp);
+                block_partial<LD, 2>(c, PART, s_warp);
             }
             if (!grid_sync(a.bar, &s_flag)) return;
-            grid_reduce<LD, 2>(a.partial, s_red);
+            grid_reduce<LD, 2>(PART, s_red);
+            ++red;
             if (threadIdx.x < LD) {
                 const int p = threadIdx.x;
                 if (s_state[p] == S_CONV_S) {
@@ -418,10 +473,11 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
                     st_vec<VEC>(a.x + vi, xv);
                     st_vec<VEC>(a.r + vi, rv);
                 ROWS_END
-                block_partial<LD, 2>(c, a.partial, s_warp);
+                block_partial<LD, 2>(c, PART, s_warp);
             }
             if (!grid_sync(a.bar, &s_flag)) return;
-            grid_reduce<LD, 2>(a.partial, s_red);
+            grid_reduce<LD, 2>(PART, s_red);
+            ++red;
             if (threadIdx.x < LD) {
                 const int p = threadIdx.x;
                 if (s_state[p] == S_ACTIVE) {
@@ -473,22 +529,24 @@ __global__ void __launch_bounds__(NT) fom_march_kernel(FomArgs a) {
     }
 #undef ROWS_BEGIN
 #undef ROWS_END
+#undef PART
 }
 
-// amu[e * LD + p] = sum_q theta[p][q] vals[q][e] (zero for padding samples);
-// x = u0 (or 0) for every sample.
+// amu[e * LD + p] = sum_q theta[p][q] vals[q][src[e]] for the mixed entries
+// (zero for padding entries and samples); x = u0 (or 0) for every sample.
 template <int LD>
-__global__ void fom_setup_kernel(int64_t ell, int Q, const double* __restrict__ vals,
-                                 const double* __restrict__ theta, int n_mu, double* amu, int64_t N,
-                                 const double* u0, double* x) {
-    const int64_t tot = ell * LD;
+__global__ void fom_setup_kernel(int64_t mx, const int64_t* __restrict__ src, int64_t ell, int Q,
+                                 const double* __restrict__ vals, const double* __restrict__ theta,
+                                 int n_mu, double* amu, int64_t N, const double* u0, double* x) {
+    const int64_t tot = mx * LD;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = i / LD;
         const int p = (int)(i % LD);
+        const int64_t se = src[e];
         double s = 0.0;
-        if (p < n_mu)
-            for (int q = 0; q < Q; ++q) s = fma(theta[p * Q + q], vals[(int64_t)q * ell + e], s);
+        if (p < n_mu && se >= 0)
+            for (int q = 0; q < Q; ++q) s = fma(theta[p * Q + q], vals[(int64_t)q * ell + se], s);
         amu[i] = s;
     }
     const int64_t totx = N * LD;
@@ -503,33 +561,39 @@ template <int LD>
 st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const double* d_dt,
                     const double* u0, int n_in, const double* B, const double* d_F, double* snap,
                     int32_t* iters, int32_t* status, int32_t* d_iters_tmp) {
-    const int64_t N = m->N, ell = m->ell_size;
+    const int64_t N = m->N, ell = m->ell_size, mx = m->mx_size;
     const size_t vec = (size_t)N * LD;
-    int blocks = st_coop_blocks(m, fom_march_kernel<LD>, NT, 0, 2);
+    int blocks = st_coop_blocks(m, fom_march_kernel<LD>, NT, 0, ST_FOM_BLOCKS_PER_SM);
     if (blocks < 1) return st_fail(ST_ERR_CUDA, "fom: cooperative occupancy query failed");
     const int64_t rpb = Cfg<LD>::RPB;
     const int64_t nchunks = (N + rpb - 1) / rpb;
     if (blocks > nchunks) blocks = (int)std::max<int64_t>(1, nchunks);
-    size_t need = sizeof(double) * ((size_t)ell * LD + 7 * vec + (size_t)blocks * NSLOT * LD) + 1024;
+    size_t need = sizeof(double) * ((size_t)mx * LD + 7 * vec + 2 * (size_t)blocks * NSLOT * LD) + 1024;
     ST_TRY(st_grow(m, m->ws_fom, need));
     double* base = (double*)m->ws_fom.p;
     double* amu = base;
-    double* vecs = amu + (size_t)ell * LD;
+    double* vecs = amu + (size_t)mx * LD;
     double* partial = vecs + 7 * vec;
-    int sblocks = (int)std::min<int64_t>((ell * LD + 255) / 256, 8 * m->num_sms);
+    int sblocks = (int)std::min<int64_t>((std::max(mx, N) * LD + 255) / 256, 8 * m->num_sms);
     {
         ST_PROF(m, "fom_setup_kernel");
         fom_setup_kernel<LD><<<std::max(sblocks, 1), 256, 0, m->stream>>>(
-            ell, m->Q, m->d_vals, d_theta, n_mu, amu, N, u0, vecs);
+            mx, m->d_mx_src, ell, m->Q, m->d_vals, d_theta, n_mu, amu, N, u0, vecs);
         ST_TRY(st_check_launch("fom_setup"));
     }
     ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, m->stream));
     FomArgs a;
     a.N = N;
-    a.slice_ptr = m->d_slice_ptr;
-    a.slice_w = m->d_slice_w;
-    a.col = m->d_col;
+    a.Q = m->Q;
+    a.theta = d_theta;
+    a.mx_ptr = m->d_mx_ptr;
+    a.mx_w = m->d_mx_w;
+    a.mx_col = m->d_mx_col;
     a.amu = amu;
+    a.tq_ptr = m->d_tq_ptr;
+    a.tq_w = m->d_tq_w;
+    a.tq_col = m->d_tq_col;
+    a.tq_val = m->d_tq_val;
     a.Nt = Nt;
     a.dt = d_dt;
     a.n_in = n_in;

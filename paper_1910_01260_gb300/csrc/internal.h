@@ -52,6 +52,20 @@ struct st_model {
     int32_t* d_slice_w = nullptr;    // [n_slices] widths
     int32_t* d_col = nullptr;        // [ell_size]
     double* d_vals = nullptr;        // [Q * ell_size]
+    // the same operator split by affine term for the full-order march:
+    // entries with several nonzero terms ("mixed", per-sample values built
+    // at march time from d_vals via d_mx_src), and per term q the entries
+    // where only term q is nonzero (one shared value, scaled by theta_q once
+    // per row).  Each group is sliced-ELL with its own widths.
+    int64_t mx_size = 0, tq_size = 0;
+    int64_t* d_mx_ptr = nullptr;  // [n_slices + 1]
+    int32_t* d_mx_w = nullptr;    // [n_slices]
+    int32_t* d_mx_col = nullptr;  // [mx_size]
+    int64_t* d_mx_src = nullptr;  // [mx_size] entry of d_vals, -1 for padding
+    int64_t* d_tq_ptr = nullptr;  // [n_slices * Q + 1]
+    int32_t* d_tq_w = nullptr;    // [n_slices * Q]
+    int32_t* d_tq_col = nullptr;  // [tq_size]
+    double* d_tq_val = nullptr;   // [tq_size]
 
     // bases
     int ns = 0, nt = 0, Nt = 0;

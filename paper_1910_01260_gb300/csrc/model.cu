@@ -238,6 +238,14 @@ void st_model_destroy(st_model* m) {
     cudaFree(m->d_slice_w);
     cudaFree(m->d_col);
     cudaFree(m->d_vals);
+    cudaFree(m->d_mx_ptr);
+    cudaFree(m->d_mx_w);
+    cudaFree(m->d_mx_col);
+    cudaFree(m->d_mx_src);
+    cudaFree(m->d_tq_ptr);
+    cudaFree(m->d_tq_w);
+    cudaFree(m->d_tq_col);
+    cudaFree(m->d_tq_val);
     cudaFree(m->d_err);
     cudaFree(m->d_bar);
     for (DevBuf* b : {&m->W, &m->V, &m->ws_fom, &m->ws_pod, &m->ws_pod2, &m->ws_gemm,
@@ -321,6 +329,75 @@ st_status st_model_create(const st_affine_csr* A, const st_options* opt, void* s
     m->n_slices = ns_;
     m->ell_size = ell;
     m->max_width = max_w;
+    // term split: group g = 0 mixed entries, g = 1 + q entries of term q only
+    // (entries with no nonzero term are dropped)
+    const int Qn = m->Q;
+    auto group_of = [&](int64_t csr_e) -> int {
+        int cnt = 0, last = 0;
+        for (int q = 0; q < Qn; ++q)
+            if (A->vals[q][csr_e] != 0.0) {
+                ++cnt;
+                last = q;
+            }
+        return cnt == 0 ? -1 : (cnt == 1 ? 1 + last : 0);
+    };
+    std::vector<int32_t> gw((size_t)ns_ * (Qn + 1), 0);
+    for (int64_t s = 0; s < ns_; ++s)
+        for (int64_t r = s * kSlice; r < std::min<int64_t>(N, (s + 1) * kSlice); ++r) {
+            std::vector<int> cnt(Qn + 1, 0);
+            for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e) {
+                const int g = group_of(e);
+                if (g >= 0) ++cnt[g];
+            }
+            for (int g = 0; g <= Qn; ++g)
+                gw[(size_t)s * (Qn + 1) + g] = std::max(gw[(size_t)s * (Qn + 1) + g], cnt[g]);
+        }
+    std::vector<int64_t> mx_ptr(ns_ + 1, 0), tq_ptr((size_t)ns_ * Qn + 1, 0);
+    std::vector<int32_t> mx_w(ns_), tq_w((size_t)ns_ * Qn);
+    for (int64_t s = 0; s < ns_; ++s) {
+        mx_w[s] = gw[(size_t)s * (Qn + 1)];
+        mx_ptr[s + 1] = mx_ptr[s] + (int64_t)mx_w[s] * kSlice;
+        for (int q = 0; q < Qn; ++q) {
+            const size_t i = (size_t)s * Qn + q;
+            tq_w[i] = gw[(size_t)s * (Qn + 1) + 1 + q];
+            tq_ptr[i + 1] = tq_ptr[i] + (int64_t)tq_w[i] * kSlice;
+        }
+    }
+    const int64_t mx_n = mx_ptr[ns_], tq_n = tq_ptr[(size_t)ns_ * Qn];
+    std::vector<int32_t> mx_col(mx_n), tq_col(tq_n);
+    std::vector<int64_t> mx_src(mx_n, -1);
+    std::vector<double> tq_val(tq_n, 0.0);
+    for (int64_t s = 0; s < ns_; ++s)
+        for (int lane = 0; lane < kSlice; ++lane) {
+            const int64_t r = s * kSlice + lane;
+            const int32_t self = r < N ? (int32_t)r : 0;
+            std::vector<int> fill(Qn + 1, 0);
+            if (r < N)
+                for (int64_t k = 0; k < A->rowptr[r + 1] - A->rowptr[r]; ++k) {
+                    const int64_t ce = A->rowptr[r] + k;
+                    const int g = group_of(ce);
+                    if (g < 0) continue;
+                    const int slot = fill[g]++;
+                    if (g == 0) {
+                        const int64_t e = mx_ptr[s] + (int64_t)slot * kSlice + lane;
+                        mx_col[e] = A->col[ce];
+                        mx_src[e] = sptr[s] + k * kSlice + lane;  // same entry in the sliced-ELL
+                    } else {
+                        const int64_t e = tq_ptr[(size_t)s * Qn + g - 1] + (int64_t)slot * kSlice + lane;
+                        tq_col[e] = A->col[ce];
+                        tq_val[e] = A->vals[g - 1][ce];
+                    }
+                }
+            for (int g = 0; g <= Qn; ++g) {
+                const int w = g == 0 ? mx_w[s] : tq_w[(size_t)s * Qn + g - 1];
+                for (int slot = fill[g]; slot < w; ++slot) {
+                    if (g == 0) mx_col[mx_ptr[s] + (int64_t)slot * kSlice + lane] = self;
+                    else tq_col[tq_ptr[(size_t)s * Qn + g - 1] + (int64_t)slot * kSlice + lane] = self;
+                }
+            }
+        }
+    m->mx_size = mx_n;
+    m->tq_size = tq_n;
     auto fail = [&](cudaError_t e) {
         st_model_destroy(m);
         return st_fail(e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA,
@@ -338,6 +415,21 @@ st_status st_model_create(const st_affine_csr* A, const st_options* opt, void* s
     if (ell > 0) {
         if ((e = cudaMemcpy(m->d_col, col.data(), sizeof(int32_t) * ell, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
         if ((e = cudaMemcpy(m->d_vals, vals.data(), sizeof(double) * m->Q * ell, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    }
+    {
+        auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+            cudaError_t ee = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+            if (ee != cudaSuccess || bytes == 0) return ee;
+            return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+        };
+        if ((e = up((void**)&m->d_mx_ptr, mx_ptr.data(), sizeof(int64_t) * mx_ptr.size())) != cudaSuccess) return fail(e);
+        if ((e = up((void**)&m->d_mx_w, mx_w.data(), sizeof(int32_t) * mx_w.size())) != cudaSuccess) return fail(e);
+        if ((e = up((void**)&m->d_mx_col, mx_col.data(), sizeof(int32_t) * mx_col.size())) != cudaSuccess) return fail(e);
+        if ((e = up((void**)&m->d_mx_src, mx_src.data(), sizeof(int64_t) * mx_src.size())) != cudaSuccess) return fail(e);
+        if ((e = up((void**)&m->d_tq_ptr, tq_ptr.data(), sizeof(int64_t) * tq_ptr.size())) != cudaSuccess) return fail(e);
+        if ((e = up((void**)&m->d_tq_w, tq_w.data(), sizeof(int32_t) * tq_w.size())) != cudaSuccess) return fail(e);
+        if ((e = up((void**)&m->d_tq_col, tq_col.data(), sizeof(int32_t) * tq_col.size())) != cudaSuccess) return fail(e);
+        if ((e = up((void**)&m->d_tq_val, tq_val.data(), sizeof(double) * tq_val.size())) != cudaSuccess) return fail(e);
     }
     if ((e = cudaMemset(m->d_err, 0, sizeof(int32_t))) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(m->d_bar, 0, sizeof(unsigned int) * 4)) != cudaSuccess) return fail(e);

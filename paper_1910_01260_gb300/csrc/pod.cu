@@ -472,6 +472,7 @@ struct JacArgs {
     int* flags;    // [3]
     int* sweeps;   // out
     double* nrm2;  // [n + 1]: squared column norms, then the largest
+    double* nsort; // [n] the norms at the start of the sweep, for the ordering
     double cut;    // relative singular-value cut below which columns are dropped
     unsigned long long* rotations;  // out: rotations applied (accumulated)
     GridBarrier bar;
@@ -539,6 +540,7 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
             acc = warp_sum(acc);
             if (lane == 0) {
                 __stcg(a.nrm2 + c, acc);
+                __stcg(a.nsort + c, acc);
                 // largest squared norm (positive doubles order like their bit patterns)
                 if (sweep == 0)
                     atomicMax(reinterpret_cast<unsigned long long*>(a.nrm2 + a.n),
@@ -547,8 +549,9 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
         }
         if (!grid_sync(a.bar, &s_flag)) return;
         // visiting order of this sweep: decreasing norm, ties by index; every
-        // CTA ranks the norms itself into shared memory
-        for (int c = tid; c < a.n; c += nthr) snrm[c] = __ldcg(a.nrm2 + c);
+        // CTA ranks the norms itself into shared memory (from a copy that the
+        // rounds of this sweep do not update)
+        for (int c = tid; c < a.n; c += nthr) snrm[c] = __ldcg(a.nsort + c);
         __syncthreads();
         for (int c = tid; c < a.n; c += nthr) {
             const double v = snrm[c];
@@ -914,7 +917,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     double* q_beta = hbuf + pdim;        // [cap] R diagonal of the pivoted QR
     double* q_tau = q_beta + cap;        // [cap] Householder coefficients
     double* q_scale = q_tau + cap;       // [cap] 1 / (x_k - beta_k)
-    double* q_nrm = q_scale + cap;       // [2 cap] trailing squared norms (double buffered)
+    double* q_nrm = q_scale + cap;       // [2 cap] QR trailing norms (double buffered), then the Jacobi sweep-start norms
     double* d_sig = q_nrm + 2 * cap;     // [cap] current sigma (device copy)
     double* d_sig_sorted = d_sig + cap;  // [cap]
     double* d_sig_tmp = d_sig_sorted + cap;
@@ -974,7 +977,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         // matrix are these columns, normalised)
         JacArgs ja{mrows, ncols, Z, cap, Y, cap, m->opt.jacobi_sweeps,
                    std::sqrt((double)mrows) * 2.220446049250313e-16, d_int + 3, d_int + 2, d_sig_tmp,
-                   0.1 * m->opt.eps_sv, d_rot, bar};
+                   q_nrm, 0.1 * m->opt.eps_sv, d_rot, bar};
         void* args[] = {&ja};
         ST_PROF(m, "jacobi_kernel");
         ST_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(jb), dim3(32 * JW), args, smem, st));
