@@ -14,7 +14,7 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(NT) dgemm_kernel(int64_t M, int64_t Nc, int64_t K, int64_t kchunk,
+__global__ void __launch_bounds__(NT, 3) dgemm_kernel(int64_t M, int64_t Nc, int64_t K, int64_t kchunk,
                                                    double alpha, const double* __restrict__ A,
                                                    int64_t lda, int64_t sA, const double* __restrict__ B,
                                                    int64_t ldb, int64_t sB, double beta, double* C,
@@ -31,6 +31,10 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(int64_t M, int64_t Nc, int64_
     C += batch * sC;
     const int64_t kb = (int64_t)split * kchunk;
     const int64_t ke = K < kb + kchunk ? K : kb + kchunk;
+    const bool full = i0 + BM <= M && j0 + BN <= Nc;
+    const int64_t rx = M - i0 - tx, ry = Nc - j0 - ty;  // valid rows / columns of this thread
+    const int nx = rx <= 0 ? 0 : (int)(rx >= 49 ? 4 : (rx + 15) / 16);
+    const int ny = ry <= 0 ? 0 : (int)(ry >= 49 ? 4 : (ry + 15) / 16);
     double acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -63,18 +67,38 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(int64_t M, int64_t Nc, int64_
             Bs[kk][jj] = v;
         }
         __syncthreads();
+        if (full) {
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            double a[4], b[4];
+            for (int kk = 0; kk < BK; ++kk) {
+                double a[4], b[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                a[t] = As[kk][tx + 16 * t];
-                b[t] = Bs[kk][ty + 16 * t];
+                for (int t = 0; t < 4; ++t) {
+                    a[t] = As[kk][tx + 16 * t];
+                    b[t] = Bs[kk][ty + 16 * t];
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
             }
+        } else {
+            // edge tile: skip the products of rows / columns past the matrix
+            // (whole warps drop out where a tile is mostly padding)
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int kk = 0; kk < BK; ++kk) {
+                double a[4], b[4];
 #pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+                for (int t = 0; t < 4; ++t) {
+                    a[t] = As[kk][tx + 16 * t];
+                    b[t] = Bs[kk][ty + 16 * t];
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+                    if (x < nx)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y)
+                            if (y < ny) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+            }
         }
         __syncthreads();
     }
@@ -122,9 +146,18 @@ st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nc,
         K = 0;
     }
     int64_t tiles = ((M + BM - 1) / BM) * ((Nc + BN - 1) / BN) * batch;
+    // split long K so that the blocks fill the resident slots in one wave
+    // (never more: a second, nearly empty wave would double the time)
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, dgemm_kernel<false, false>, NT, 0) != cudaSuccess) v = 1;
+        per_sm = std::max(1, v);
+    }
+    const int64_t slots = (int64_t)per_sm * m->num_sms;
     int splits = 1;
-    if (batch == 1 && K > 2048 && tiles < 2 * m->num_sms) {
-        int64_t want = (2 * m->num_sms + tiles - 1) / tiles;
+    if (batch == 1 && K > 2048 && 2 * tiles <= slots) {
+        int64_t want = slots / tiles;
         want = std::min<int64_t>(want, K / 512);
         splits = (int)std::max<int64_t>(1, std::min<int64_t>(want, 64));
     }

@@ -52,6 +52,7 @@ struct FomArgs {
     const double* B;  // [N x n_in]
     const double* F;  // [Nt x n_in]
     double *x, *r, *rh, *p, *v, *s, *t;  // [N * LD]
+    double* hist;                        // [3 x N * LD] solutions of the last three levels
     double* partial;                     // [2 x grid * NSLOT * LD]
     double* snap;
     int n_mu;
@@ -229,9 +230,39 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
         const int64_t vi = row * LD + p0;
 #define ROWS_END }
 
+    const size_t vecsz = (size_t)N * LD;
+    // level 0 (u0) into the history, on this block's rows
+    ROWS_BEGIN
+        double xv[VEC];
+        ld_vec<VEC>(a.x + vi, xv);
+        st_vec<VEC>(a.hist + vi, xv);
+    ROWS_END
     for (int k = 0; k < a.Nt; ++k) {
         const double h = a.dt[k];
-        // ---- Phase R: b = u + h B f^k, r = b - K u = h (B f^k + A u), r^ = r
+        const double* uk = a.hist + (size_t)(k % 3) * vecsz;  // the previous level u^k
+        // ---- Phase X0: initial iterate by extrapolating the last levels in
+        // time (quadratic from the third step on), which only shortens the
+        // Krylov iteration; the stopping test is on the true system
+        if (k > 0) {
+            const double* ukm1 = a.hist + (size_t)((k + 2) % 3) * vecsz;
+            const double* ukm2 = a.hist + (size_t)((k + 1) % 3) * vecsz;
+            ROWS_BEGIN
+                double x0[VEC], u1[VEC], u2[VEC];
+                ld_vec<VEC>(uk + vi, x0);
+                ld_vec<VEC>(ukm1 + vi, u1);
+                if (k > 1) {
+                    ld_vec<VEC>(ukm2 + vi, u2);
+#pragma unroll
+                    for (int u = 0; u < VEC; ++u) x0[u] = fma(3.0, x0[u] - u1[u], u2[u]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < VEC; ++u) x0[u] = fma(2.0, x0[u], -u1[u]);
+                }
+                st_vec<VEC>(a.x + vi, x0);
+            ROWS_END
+            if (!grid_sync(a.bar, &s_flag)) return;
+        }
+        // ---- Phase R: b = u^k + h B f^k, r = b - K x0 = b - x0 + h A x0, r^ = r
         {
             double c[NSLOT][VEC];
 #pragma unroll
@@ -239,15 +270,16 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
             ROWS_BEGIN
                 double bf = 0.0;
                 for (int s = 0; s < a.n_in; ++s) bf = fma(__ldg(a.B + row + (int64_t)s * N), __ldg(a.F + (int64_t)k * a.n_in + s), bf);
-                double Au[VEC], xv[VEC];
+                double Au[VEC], xv[VEC], ukv[VEC];
                 spmv_A<LD>(a, row, p0, a.x, s_theta, Au);
                 ld_vec<VEC>(a.x + vi, xv);
+                ld_vec<VEC>(uk + vi, ukv);
                 double rr[VEC], zero[VEC];
 #pragma unroll
                 for (int u = 0; u < VEC; ++u) {
                     const bool on = s_state[p0 + u] != S_FAILED && s_state[p0 + u] != S_PAD;
-                    const double b = xv[u] + h * bf;
-                    rr[u] = on ? h * (bf + Au[u]) : 0.0;
+                    const double b = fma(h, bf, ukv[u]);
+                    rr[u] = on ? fma(h, Au[u], b - xv[u]) : 0.0;
                     zero[u] = 0.0;
                     if (on) {
                         c[0][u] = fma(b, b, c[0][u]);
@@ -513,6 +545,7 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
                 if (p < a.n_mu) __stcs(a.snap + ((int64_t)p * a.Nt + k) * N + row, xv[u]);
             }
             if (changed) st_vec<VEC>(a.x + vi, xv);
+            st_vec<VEC>(a.hist + (size_t)((k + 1) % 3) * vecsz + vi, xv);
         ROWS_END
         if (blockIdx.x == 0 && threadIdx.x < a.n_mu) {
             const int p = threadIdx.x;
@@ -568,12 +601,12 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     const int64_t rpb = Cfg<LD>::RPB;
     const int64_t nchunks = (N + rpb - 1) / rpb;
     if (blocks > nchunks) blocks = (int)std::max<int64_t>(1, nchunks);
-    size_t need = sizeof(double) * ((size_t)mx * LD + 7 * vec + 2 * (size_t)blocks * NSLOT * LD) + 1024;
+    size_t need = sizeof(double) * ((size_t)mx * LD + 10 * vec + 2 * (size_t)blocks * NSLOT * LD) + 1024;
     ST_TRY(st_grow(m, m->ws_fom, need));
     double* base = (double*)m->ws_fom.p;
     double* amu = base;
     double* vecs = amu + (size_t)mx * LD;
-    double* partial = vecs + 7 * vec;
+    double* partial = vecs + 10 * vec;
     int sblocks = (int)std::min<int64_t>((std::max(mx, N) * LD + 255) / 256, 8 * m->num_sms);
     {
         ST_PROF(m, "fom_setup_kernel");
@@ -606,6 +639,7 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     a.v = vecs + 4 * vec;
     a.s = vecs + 5 * vec;
     a.t = vecs + 6 * vec;
+    a.hist = vecs + 7 * vec;
     a.partial = partial;
     a.snap = snap;
     a.n_mu = n_mu;

@@ -87,15 +87,14 @@ struct Gs2Args {
     double* P;      // m x m (ld m), zeroed by the host
     int* k_out;
     const double* tau;  // NULL: every column adds a direction
-    double* partial;    // [grid x m]
-    double* hbuf;       // [m]
+    double* partial;    // [2 x grid x (m + 1)]
     GridBarrier bar;
 };
 
 __global__ void __launch_bounds__(NT) gs2_kernel(Gs2Args a) {
     extern __shared__ double sm[];
-    double* h = sm;          // [m]
-    double* h2 = sm + a.m;   // [m]
+    double* h = sm;          // [m] first-pass coefficients
+    double* h2 = sm + a.m;   // [m] second-pass coefficients
     __shared__ double s_part[NWARP];
     __shared__ double s_nu;
     __shared__ int s_flag;
@@ -104,64 +103,80 @@ __global__ void __launch_bounds__(NT) gs2_kernel(Gs2Args a) {
     const int64_t R = (a.N + G - 1) / G;
     const int64_t r0 = (int64_t)b * R, r1 = min(a.N, r0 + R);
     const double tau = a.tau ? *a.tau : -1.0;
+    // Every block owns rows [r0, r1) of E and J: the updates are local and
+    // only the dot products cross blocks.  Each reduction writes per-block
+    // partials to one of two buffers (alternating) and every block sums all
+    // of them in a fixed order, so a buffer is rewritten only two barriers
+    // after it was read: three barriers per column.
+    int red = 0;
+    auto part = [&](int slot) { return a.partial + ((size_t)(red & 1) * G + b) * (a.m + 1) + slot; };
+    auto part_of = [&](int bb, int slot) { return a.partial + ((size_t)(red & 1) * G + bb) * (a.m + 1) + slot; };
     int k = 0;
     for (int j = 0; j < a.m; ++j) {
         double* e = a.E + (int64_t)j * a.N;
         for (int pass = 0; pass < 2; ++pass) {
             double* hh = pass == 0 ? h : h2;
-            if (k > 0) {
-                // partial projections J(:, c)^T e over this block's rows
-                for (int c = warp; c < k; c += NWARP) {
-                    const double* jc = a.J + (int64_t)c * a.N;
-                    double acc = 0.0;
-                    for (int64_t i = r0 + lane; i < r1; i += 32) acc = fma(__ldcg(jc + i), __ldcg(e + i), acc);
-                    acc = warp_sum(acc);
-                    if (lane == 0) __stcg(a.partial + (int64_t)b * a.m + c, acc);
-                }
-                if (!grid_sync(a.bar, &s_flag)) return;
-                // level-2: block b sums entries c = b, b + G, ...
-                for (int c = b + warp * G; c < k; c += NWARP * G) {
-                    double acc = 0.0;
-                    for (int bb = lane; bb < G; bb += 32) acc += __ldcg(a.partial + (int64_t)bb * a.m + c);
-                    acc = warp_sum(acc);
-                    if (lane == 0) __stcg(a.hbuf + c, acc);
-                }
-                if (!grid_sync(a.bar, &s_flag)) return;
-                for (int c = threadIdx.x; c < k; c += NT) hh[c] = __ldcg(a.hbuf + c);
-                __syncthreads();
-                // e -= J h
-                for (int64_t i = r0 + threadIdx.x; i < r1; i += NT) {
-                    double v = __ldcg(e + i);
-                    for (int c = 0; c < k; ++c) v = fma(-__ldcg(a.J + (int64_t)c * a.N + i), hh[c], v);
-                    __stcg(e + i, v);
-                }
-                // the next pass reads e with a lane-per-row mapping
-                __syncthreads();
-            } else {
+            if (k == 0) {
                 for (int c = threadIdx.x; c < a.m; c += NT) hh[c] = 0.0;
+                continue;
             }
+            // partial projections J(:, c)^T e over this block's rows
+            for (int c = warp; c < k; c += NWARP) {
+                const double* jc = a.J + (int64_t)c * a.N;
+                double acc = 0.0;
+                for (int64_t i = r0 + lane; i < r1; i += 32) acc = fma(__ldcg(jc + i), __ldcg(e + i), acc);
+                acc = warp_sum(acc);
+                if (lane == 0) __stcg(part(c), acc);
+            }
+            if (!grid_sync(a.bar, &s_flag)) return;
+            // every block sums the partials of all blocks, fixed order
+            for (int c = warp; c < k; c += NWARP) {
+                double acc = 0.0;
+                for (int bb = lane; bb < G; bb += 32) acc += __ldcg(part_of(bb, c));
+                acc = warp_sum(acc);
+                if (lane == 0) hh[c] = acc;
+            }
+            ++red;
+            __syncthreads();
+            // e -= J h on this block's rows; after the second pass also the
+            // partial of ||e||^2
+            double nacc = 0.0;
+            for (int64_t i = r0 + threadIdx.x; i < r1; i += NT) {
+                double v = __ldcg(e + i);
+                for (int c = 0; c < k; ++c) v = fma(-__ldcg(a.J + (int64_t)c * a.N + i), hh[c], v);
+                __stcg(e + i, v);
+                nacc = fma(v, v, nacc);
+            }
+            if (pass == 1) {
+                nacc = warp_sum(nacc);
+                if (lane == 0) s_part[warp] = nacc;
+            }
+            __syncthreads();
         }
-        // ||e||^2
-        double acc = 0.0;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += NT) {
-            const double v = __ldcg(e + i);
-            acc = fma(v, v, acc);
+        if (k == 0) {
+            // no direction yet: the remainder is the column itself
+            double nacc = 0.0;
+            for (int64_t i = r0 + threadIdx.x; i < r1; i += NT) {
+                const double v = __ldcg(e + i);
+                nacc = fma(v, v, nacc);
+            }
+            nacc = warp_sum(nacc);
+            if (lane == 0) s_part[warp] = nacc;
+            __syncthreads();
         }
-        acc = warp_sum(acc);
-        if (lane == 0) s_part[warp] = acc;
-        __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;
             for (int w = 0; w < NWARP; ++w) s += s_part[w];
-            __stcg(a.partial + (int64_t)b * a.m, s);
+            __stcg(part(a.m), s);
         }
         if (!grid_sync(a.bar, &s_flag)) return;
         if (warp == 0) {
             double s = 0.0;
-            for (int bb = lane; bb < G; bb += 32) s += __ldcg(a.partial + (int64_t)bb * a.m);
+            for (int bb = lane; bb < G; bb += 32) s += __ldcg(part_of(bb, a.m));
             s = warp_sum(s);
             if (lane == 0) s_nu = sqrt(s);
         }
+        ++red;
         __syncthreads();
         const double nu = s_nu;
         if (!isfinite(nu)) {
@@ -177,8 +192,8 @@ __global__ void __launch_bounds__(NT) gs2_kernel(Gs2Args a) {
             if (b == 0 && threadIdx.x == 0) a.P[k + (int64_t)j * a.m] = nu;
             ++k;
         }
-        // the partial buffer is reused next column: all blocks must have read it
-        if (!grid_sync(a.bar, &s_flag)) return;
+        // J(:, k-1) is read next column only on this block's own rows
+        __syncthreads();
     }
     if (b == 0 && threadIdx.x == 0) *a.k_out = k;
 }
@@ -895,7 +910,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         gs_blocks = std::max(1, std::min(per_sm, 1)) * m->num_sms;
         gs_blocks = (int)std::min<int64_t>(gs_blocks, std::max<int64_t>(1, N / 64));
     }
-    const size_t szPart = std::max((size_t)std::max(gs_blocks, 1) * pdim, (size_t)64 * Nt);
+    const size_t szPart = std::max((size_t)2 * std::max(gs_blocks, 1) * (pdim + 1), (size_t)64 * Nt);
     const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 3 * szX + (size_t)cap * rmax * 2 +
                            szPart + pdim + 9 * cap + 32;
     ST_TRY(st_grow(m, m->ws_pod, sizeof(double) * doubles + sizeof(int) * (2 * cap + 16)));
@@ -913,8 +928,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     double* Ysel = Z + szX;
     double* Vsel = Ysel + (size_t)cap * rmax;
     double* partial = Vsel + (size_t)cap * rmax;
-    double* hbuf = partial + szPart;
-    double* q_beta = hbuf + pdim;        // [cap] R diagonal of the pivoted QR
+    double* q_beta = partial + szPart;   // [cap] R diagonal of the pivoted QR
     double* q_tau = q_beta + cap;        // [cap] Householder coefficients
     double* q_scale = q_tau + cap;       // [cap] 1 / (x_k - beta_k)
     double* q_nrm = q_scale + cap;       // [2 cap] QR trailing norms (double buffered), then the Jacobi sweep-start norms
@@ -990,7 +1004,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     auto run_gs = [&](double* Ein, int mcols, double* Jout, double* Pout, const double* tau) -> st_status {
         ST_CUDA_TRY(cudaMemsetAsync(Pout, 0, sizeof(double) * (size_t)mcols * mcols, st));
         ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
-        Gs2Args g{N, mcols, Ein, Jout, Pout, d_int, tau, partial, hbuf, bar};
+        Gs2Args g{N, mcols, Ein, Jout, Pout, d_int, tau, partial, bar};
         void* args[] = {&g};
         ST_PROF(m, "gs2_kernel");
         ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT), args,
@@ -1140,7 +1154,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
                 ++m->pod_reorth;
                 ST_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)r * r, st));
                 ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
-                Gs2Args g{N, r, W, W2, P, d_int, nullptr, partial, hbuf, bar};
+                Gs2Args g{N, r, W, W2, P, d_int, nullptr, partial, bar};
                 void* args[] = {&g};
                 ST_PROF(m, "gs2_kernel");
                 ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT),

@@ -55,6 +55,8 @@ struct Smem {
     double* x;    // solution
     double* r;    // residual / correction
     int* piv;     // pivots
+    int* perm;    // row permutation of the pivots (row i of P A is row perm[i] of A)
+    T* D;         // 2 x 32 x 32 diagonal blocks for the triangular solves
 };
 
 __device__ __forceinline__ void block_argmax(double v, int idx, double* s_val, int* s_idx,
@@ -234,39 +236,103 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, double* s_v
     return ok;
 }
 
-// x <- A^{-1} x using the LU factors and pivots in A / s.piv (factors in T,
-// x in FP64; with T = float the products are rounded to FP32 factors' accuracy).
+// perm from the pivot sequence (one thread): the row interchanges applied in
+// order to the identity.
+__device__ __forceinline__ void lu_perm(int n, const int* piv, int* perm) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = 0; i < n; ++i) {
+        const int pr = piv[i];
+        if (pr != i) {
+            const int t = perm[i];
+            perm[i] = perm[pr];
+            perm[pr] = t;
+        }
+    }
+}
+
+// Diagonal 32 x 32 block of A at (c0, c0), zero outside the w x w block.
+template <typename T>
+__device__ __forceinline__ void load_diag(const T* A, int n, int c0, int w, T* D) {
+    for (int t = threadIdx.x; t < 32 * 32; t += NT) {
+        const int r = t & 31, c = t >> 5;
+        D[t] = (r < w && c < w) ? A[(c0 + r) + (int64_t)(c0 + c) * n] : (T)0;
+    }
+}
+
+// x <- A^{-1} x using the LU factors in A and s.perm (factors in T, x in
+// FP64; with T = float the products are rounded to the FP32 factors'
+// accuracy).  Blocked substitution: warp 0 solves each 32 x 32 diagonal
+// block (staged in shared memory) with shuffles, then all threads update the
+// rest of x with the block's 32 new entries while the next diagonal block is
+// staged -- two block barriers per 32 columns.
 template <typename T>
 __device__ void lu_solve(const T* A, int n, Smem<T>& s, double* x) {
-    const int tid = threadIdx.x;
-    if (tid == 0)
-        for (int i = 0; i < n; ++i) {
-            const int pr = s.piv[i];
-            if (pr != i) {
-                const double t = x[i];
-                x[i] = x[pr];
-                x[pr] = t;
-            }
-        }
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double* tmp = reinterpret_cast<double*>(s.P);  // the panel is free after the factorisation
+    for (int i = tid; i < n; i += NT) tmp[i] = x[s.perm[i]];
+    load_diag(A, n, 0, min(32, n), s.D);
     __syncthreads();
-    for (int c = 0; c < n; ++c) {
-        const double xc = x[c];
-        for (int r = c + 1 + tid; r < n; r += NT) x[r] = fma(-(double)A[r + (int64_t)c * n], xc, x[r]);
+    for (int i = tid; i < n; i += NT) x[i] = tmp[i];
+    __syncthreads();
+    // L y = P x, L unit lower triangular
+    int buf = 0;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int w = min(32, n - c0);
+        const T* D = s.D + buf * 1024;
+        if (warp == 0) {
+            double xr = lane < w ? x[c0 + lane] : 0.0;
+            for (int c = 0; c < w - 1; ++c) {
+                const double xc = __shfl_sync(0xffffffffu, xr, c);
+                if (lane > c) xr = fma(-(double)D[lane + 32 * c], xc, xr);
+            }
+            if (lane < w) x[c0 + lane] = xr;
+        }
+        __syncthreads();
+        if (c0 + 32 < n) load_diag(A, n, c0 + 32, min(32, n - c0 - 32), s.D + (buf ^ 1) * 1024);
+        for (int r = c0 + w + tid; r < n; r += NT) {
+            double acc = x[r];
+            for (int c = 0; c < w; ++c) acc = fma(-(double)A[r + (int64_t)(c0 + c) * n], x[c0 + c], acc);
+            x[r] = acc;
+        }
+        buf ^= 1;
         __syncthreads();
     }
-    for (int c = n - 1; c >= 0; --c) {
-        if (tid == 0) x[c] /= (double)A[c + (int64_t)c * n];
+    // U x = y, from the last block up
+    {
+        const int c1 = n, c0 = c1 > 32 ? c1 - 32 : 0;
+        load_diag(A, n, c0, c1 - c0, s.D + buf * 1024);
         __syncthreads();
-        const double xc = x[c];
-        for (int r = tid; r < c; r += NT) x[r] = fma(-(double)A[r + (int64_t)c * n], xc, x[r]);
+    }
+    for (int c1 = n; c1 > 0; c1 -= 32) {
+        const int c0 = c1 > 32 ? c1 - 32 : 0, w = c1 - c0;
+        const T* D = s.D + buf * 1024;
+        if (warp == 0) {
+            double xr = lane < w ? x[c0 + lane] : 0.0;
+            for (int c = w - 1; c >= 0; --c) {
+                if (lane == c) xr = xr / (double)D[c + 32 * c];
+                const double xc = __shfl_sync(0xffffffffu, xr, c);
+                if (lane < c) xr = fma(-(double)D[lane + 32 * c], xc, xr);
+            }
+            if (lane < w) x[c0 + lane] = xr;
+        }
+        __syncthreads();
+        if (c0 > 0) {
+            const int n0 = c0 > 32 ? c0 - 32 : 0;
+            load_diag(A, n, n0, c0 - n0, s.D + (buf ^ 1) * 1024);
+        }
+        for (int r = tid; r < c0; r += NT) {
+            double acc = x[r];
+            for (int c = 0; c < w; ++c) acc = fma(-(double)A[r + (int64_t)(c0 + c) * n], x[c0 + c], acc);
+            x[r] = acc;
+        }
+        buf ^= 1;
         __syncthreads();
     }
 }
 
-// Entry (row, col) of the sample's Ahat^st in FP64 (row = i' + a j', col = i + a j).
-__device__ __forceinline__ double st_entry(const SolveArgs& g, const double* Ah, int a, int row,
-                                           int col) {
-    const int ip = row % a, jp = row / a, i = col % a, j = col / a;
+// Entry ((i',j'),(i,j)) of the sample's Ahat^st in FP64 (row i' + a j', column i + a j).
+__device__ __forceinline__ double st_entry(const SolveArgs& g, const double* Ah, int a, int ip, int jp,
+                                           int i, int j) {
     const int64_t gi = (int64_t)(ip + g.ns * jp) + (int64_t)(i + g.ns * j) * g.nfull;
     double v = -Ah[ip + i * a] * g.G[gi];
     if (ip == i) {
@@ -279,7 +345,7 @@ __device__ __forceinline__ double st_entry(const SolveArgs& g, const double* Ah,
 // T: arithmetic of the assembled matrix and its LU factors (double, or
 // float for the FP32-factorisation mode); residuals and the solution are FP64.
 template <typename T>
-__global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
+__global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
     extern __shared__ double smem[];
     __shared__ double s_val[NWARP];
     __shared__ int s_idx[NWARP];
@@ -293,6 +359,12 @@ __global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
     s.x = s.b + nfull;
     s.r = s.x + nfull;
     s.piv = reinterpret_cast<int*>(s.r + nfull);
+    s.perm = s.piv + nfull;
+    {
+        // 16-byte aligned after the index arrays
+        const uintptr_t pd = (reinterpret_cast<uintptr_t>(s.perm + nfull) + 15) & ~(uintptr_t)15;
+        s.D = reinterpret_cast<T*>(pd);
+    }
     T* A = reinterpret_cast<T*>(g.ws) + (size_t)blockIdx.x * nfull * nfull;
     const int tid = threadIdx.x;
     for (;;) {
@@ -330,6 +402,7 @@ __global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
         for (int t = tid; t < n; t += NT) {
             const int i = t % a, j = t / a;
             s.b[t] = g.rhs[i + g.ns * j];
+            s.perm[t] = i | (j << 16);  // (i, j) of index t, until the factorisation
         }
         __syncthreads();
         // assemble Ahat^st (FP64, or FP32 products in the FP32-assembly mode)
@@ -337,7 +410,8 @@ __global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
             const int row = (int)(t % n), col = (int)(t / n);
             T v;
             if (g.fp32_asm) {
-                const int ip = row % a, jp = row / a, i = col % a, j = col / a;
+                const int rc = s.perm[row], cc = s.perm[col];
+                const int ip = rc & 0xffff, jp = rc >> 16, i = cc & 0xffff, j = cc >> 16;
                 const int64_t gi = (int64_t)(ip + g.ns * jp) + (int64_t)(i + g.ns * j) * nfull;
                 float f = -(float)s.Ah[ip + i * a] * g.G32[gi];
                 if (ip == i) {
@@ -346,7 +420,8 @@ __global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
                 }
                 v = (T)f;
             } else {
-                v = (T)st_entry(g, s.Ah, a, row, col);
+                const int rc = s.perm[row], cc = s.perm[col];
+                v = (T)st_entry(g, s.Ah, a, rc & 0xffff, rc >> 16, cc & 0xffff, cc >> 16);
             }
             A[row + (int64_t)col * n] = v;
         }
@@ -362,15 +437,27 @@ __global__ void __launch_bounds__(NT) solve_kernel(SolveArgs g) {
             __syncthreads();
             continue;
         }
+        if (tid == 0) lu_perm(n, s.piv, s.perm);
         for (int t = tid; t < n; t += NT) s.x[t] = s.b[t];
         __syncthreads();
         lu_solve(A, n, s, s.x);
         double rn = 0.0;
         for (int step = 0; step <= g.refine; ++step) {
-            // r = b - Ahat^st x (FP64, matrix regenerated from the reduced operators)
+            // r = b - Ahat^st x (FP64, matrix regenerated from the reduced
+            // operators: entry ((i',j'),(i,j)) = delta_{i'i} (M_i - S_i)[j',j]
+            // - Ahat[i',i] G[(i',j'),(i,j)], columns visited j-major)
             for (int row = tid; row < n; row += NT) {
+                const int ip = row % a, jp = row / a;
                 double acc = s.b[row];
-                for (int col = 0; col < n; ++col) acc = fma(-st_entry(g, s.Ah, a, row, col), s.x[col], acc);
+                const double* Gr = g.G + (ip + (int64_t)g.ns * jp);
+                const double* Ahr = s.Ah + ip;
+                const int64_t mi = (int64_t)ip * g.nt * g.nt + jp;
+                for (int j = 0; j < bt; ++j) {
+                    const double* Gc = Gr + (int64_t)g.ns * j * g.nfull;
+                    const double* xj = s.x + a * j;
+                    for (int i = 0; i < a; ++i) acc = fma(Ahr[i * a] * Gc[(int64_t)i * g.nfull], xj[i], acc);
+                    acc = fma(-(g.M[mi + (int64_t)j * g.nt] - g.S[mi + (int64_t)j * g.nt]), xj[ip], acc);
+                }
                 s.r[row] = acc;
             }
             __syncthreads();
@@ -430,8 +517,10 @@ __global__ void size_scatter_kernel(int n_mu, const int* __restrict__ npv, int* 
 
 // Dynamic shared memory of solve_kernel<T> for panel width nb.
 size_t solve_smem(int nfull, int ns, int nb, size_t tsize) {
-    return tsize * ((size_t)nfull * nb + (size_t)nb * CW) +
-           sizeof(double) * ((size_t)ns * ns + 3 * (size_t)nfull) + sizeof(int) * (size_t)nfull + 64;
+    // the panel also holds one FP64 vector during the triangular solves
+    const size_t panel = std::max(tsize * (size_t)nfull * nb, sizeof(double) * (size_t)nfull);
+    return panel + tsize * (size_t)nb * CW + sizeof(double) * ((size_t)ns * ns + 3 * (size_t)nfull) +
+           2 * sizeof(int) * (size_t)nfull + 16 + tsize * 2 * 32 * 32 + 64;
 }
 
 bool fp32_factors(const st_model* m) { return m->opt.precision == ST_FP32_LU; }
