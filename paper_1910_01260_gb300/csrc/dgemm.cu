@@ -157,9 +157,20 @@ st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nc,
     const int64_t slots = (int64_t)per_sm * m->num_sms;
     int splits = 1;
     if (batch == 1 && K > 2048 && 2 * tiles <= slots) {
-        int64_t want = slots / tiles;
-        want = std::min<int64_t>(want, K / 512);
-        splits = (int)std::max<int64_t>(1, std::min<int64_t>(want, 64));
+        // FP64 issue is the bound, so the time follows the SM with the most
+        // blocks: pick the split that balances blocks over the SMs best
+        // (at most one resident wave, K chunks of at least 256)
+        const int64_t cap = std::min<int64_t>(512, K / 256);
+        double best = -1.0;
+        for (int64_t sp = 1; sp <= cap && tiles * sp <= slots; ++sp) {
+            const int64_t blocks = tiles * sp;
+            const int64_t per = (blocks + m->num_sms - 1) / m->num_sms;
+            const double eff = (double)blocks / (double)(per * m->num_sms);
+            if (eff > best + 1e-9) {
+                best = eff;
+                splits = (int)sp;
+            }
+        }
     }
     int64_t kchunk = K > 0 ? ((K + splits - 1) / splits + BK - 1) / BK * BK : 0;
     if (K > 0) splits = (int)((K + kchunk - 1) / kchunk);

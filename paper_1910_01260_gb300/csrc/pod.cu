@@ -87,40 +87,126 @@ struct Gs2Args {
     double* P;      // m x m (ld m), zeroed by the host
     int* k_out;
     const double* tau;  // NULL: every column adds a direction
-    double* partial;    // [2 x grid x (m + 1)]
+    double* partial;    // [2 x grid x (m + 2)]
     GridBarrier bar;
 };
 
-__global__ void __launch_bounds__(NT) gs2_kernel(Gs2Args a) {
+__global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
     extern __shared__ double sm[];
-    double* h = sm;          // [m] first-pass coefficients
-    double* h2 = sm + a.m;   // [m] second-pass coefficients
-    __shared__ double s_part[NWARP];
-    __shared__ double s_nu;
+    // pass-1 / pass-2 coefficients of the column being finished (hc, h2c)
+    // and of the column being projected (hn, h2n); swapped every column
+    double* hc = sm;
+    double* h2c = sm + a.m;
+    double* hn = sm + 2 * (size_t)a.m;
+    double* h2n = sm + 3 * (size_t)a.m;
+    __shared__ double s_w1[NWARP], s_w2[NWARP];
+    __shared__ double s_nu, s_cross;
     __shared__ int s_flag;
     const int G = gridDim.x, b = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t R = (a.N + G - 1) / G;
     const int64_t r0 = (int64_t)b * R, r1 = min(a.N, r0 + R);
     const double tau = a.tau ? *a.tau : -1.0;
-    // Every block owns rows [r0, r1) of E and J: the updates are local and
-    // only the dot products cross blocks.  Each reduction writes per-block
-    // partials to one of two buffers (alternating) and every block sums all
-    // of them in a fixed order, so a buffer is rewritten only two barriers
-    // after it was read: three barriers per column.
+    // Every block owns rows [r0, r1) of E and J: updates are local and only
+    // dot products cross blocks.  A reduction writes per-block partials
+    // (slots 0..m-1 dots, m the squared norm, m+1 the cross term) to one of
+    // two buffers, alternating, and every block sums all blocks' partials in
+    // a fixed order, so a buffer is rewritten only two barriers after it was
+    // read.  The norm of column j, its product with column j+1 and the
+    // first-pass projections of column j+1 share one reduction (the
+    // coefficient on a direction accepted from column j is e_j^T e_{j+1} /
+    // ||e_j||): two grid barriers per column.
+    const int S = a.m + 2;
     int red = 0;
-    auto part = [&](int slot) { return a.partial + ((size_t)(red & 1) * G + b) * (a.m + 1) + slot; };
-    auto part_of = [&](int bb, int slot) { return a.partial + ((size_t)(red & 1) * G + bb) * (a.m + 1) + slot; };
-    int k = 0;
-    for (int j = 0; j < a.m; ++j) {
-        double* e = a.E + (int64_t)j * a.N;
-        for (int pass = 0; pass < 2; ++pass) {
-            double* hh = pass == 0 ? h : h2;
-            if (k == 0) {
-                for (int c = threadIdx.x; c < a.m; c += NT) hh[c] = 0.0;
-                continue;
+    auto part = [&](int slot) { return a.partial + ((size_t)(red & 1) * G + b) * S + slot; };
+    auto part_of = [&](int bb, int slot) { return a.partial + ((size_t)(red & 1) * G + bb) * S + slot; };
+    // block sums of two per-thread values, written by thread 0 to slots m, m+1
+    auto write_pair = [&](double v1, double v2) {
+        v1 = warp_sum(v1);
+        v2 = warp_sum(v2);
+        if (lane == 0) {
+            s_w1[warp] = v1;
+            s_w2[warp] = v2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int w = 0; w < NWARP; ++w) {
+                t1 += s_w1[w];
+                t2 += s_w2[w];
             }
-            // partial projections J(:, c)^T e over this block's rows
+            __stcg(part(a.m), t1);
+            __stcg(part(a.m + 1), t2);
+        }
+    };
+    int k = 0;   // directions found so far
+    int kc = 0;  // directions the finishing column was projected on
+    {
+        // column 0 has nothing to project: ||e_0||^2 and e_0^T e_1
+        const double* e0 = a.E;
+        const double* e1 = a.m > 1 ? a.E + a.N : nullptr;
+        double n2 = 0.0, cr = 0.0;
+        for (int64_t i = r0 + tid; i < r1; i += NT) {
+            const double v = __ldcg(e0 + i);
+            n2 = fma(v, v, n2);
+            if (e1) cr = fma(v, __ldcg(e1 + i), cr);
+        }
+        write_pair(n2, cr);
+    }
+    for (int j = 0; j < a.m; ++j) {
+        // reduction A: ||e_j||^2, e_j^T e_{j+1}, J(:, 0:k)^T e_{j+1}
+        if (!grid_sync(a.bar, &s_flag)) return;
+        const int kn = k;
+        for (int c = warp; c < kn; c += NWARP) {
+            double acc = 0.0;
+            for (int bb = lane; bb < G; bb += 32) acc += __ldcg(part_of(bb, c));
+            acc = warp_sum(acc);
+            if (lane == 0) hn[c] = acc;
+        }
+        if (warp == 0) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int bb = lane; bb < G; bb += 32) {
+                s1 += __ldcg(part_of(bb, a.m));
+                s2 += __ldcg(part_of(bb, a.m + 1));
+            }
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            if (lane == 0) {
+                s_nu = sqrt(s1);
+                s_cross = s2;
+            }
+        }
+        ++red;
+        __syncthreads();
+        const double nu = s_nu;
+        if (!isfinite(nu)) {
+            if (tid == 0) grid_abort(a.bar, ST_ERR_NONFINITE);
+            return;
+        }
+        // finish column j: its coefficients, and a new direction if the
+        // remainder is above the threshold
+        if (b == 0)
+            for (int c = tid; c < kc; c += NT) a.P[c + (int64_t)j * a.m] = hc[c] + h2c[c];
+        const double* ej = a.E + (int64_t)j * a.N;
+        if (nu > tau && nu > 0.0) {
+            const double inv = 1.0 / nu;
+            double* jk = a.J + (int64_t)k * a.N;
+            for (int64_t i = r0 + tid; i < r1; i += NT) __stcg(jk + i, __ldcg(ej + i) * inv);
+            if (b == 0 && tid == 0) a.P[k + (int64_t)j * a.m] = nu;
+            if (tid == 0) hn[k] = s_cross * inv;
+            ++k;
+        }
+        __syncthreads();
+        if (j + 1 == a.m) break;
+        // column j+1: first pass e -= J(:, 0:k) hn, second-pass projections
+        double* e = a.E + (int64_t)(j + 1) * a.N;
+        if (k > 0) {
+            for (int64_t i = r0 + tid; i < r1; i += NT) {
+                double v = __ldcg(e + i);
+                for (int c = 0; c < k; ++c) v = fma(-__ldcg(a.J + (int64_t)c * a.N + i), hn[c], v);
+                __stcg(e + i, v);
+            }
+            __syncthreads();
             for (int c = warp; c < k; c += NWARP) {
                 const double* jc = a.J + (int64_t)c * a.N;
                 double acc = 0.0;
@@ -128,74 +214,48 @@ __global__ void __launch_bounds__(NT) gs2_kernel(Gs2Args a) {
                 acc = warp_sum(acc);
                 if (lane == 0) __stcg(part(c), acc);
             }
+            // reduction B: J(:, 0:k)^T e_{j+1} (second pass)
             if (!grid_sync(a.bar, &s_flag)) return;
-            // every block sums the partials of all blocks, fixed order
             for (int c = warp; c < k; c += NWARP) {
                 double acc = 0.0;
                 for (int bb = lane; bb < G; bb += 32) acc += __ldcg(part_of(bb, c));
                 acc = warp_sum(acc);
-                if (lane == 0) hh[c] = acc;
+                if (lane == 0) h2n[c] = acc;
             }
             ++red;
             __syncthreads();
-            // e -= J h on this block's rows; after the second pass also the
-            // partial of ||e||^2
-            double nacc = 0.0;
-            for (int64_t i = r0 + threadIdx.x; i < r1; i += NT) {
-                double v = __ldcg(e + i);
-                for (int c = 0; c < k; ++c) v = fma(-__ldcg(a.J + (int64_t)c * a.N + i), hh[c], v);
+        }
+        kc = k;
+        // second-pass update of e_{j+1} with its squared norm and its product
+        // with e_{j+2}, and the first-pass projections of e_{j+2}
+        const double* e2 = j + 2 < a.m ? a.E + (int64_t)(j + 2) * a.N : nullptr;
+        double n2 = 0.0, cr = 0.0;
+        for (int64_t i = r0 + tid; i < r1; i += NT) {
+            double v = __ldcg(e + i);
+            if (k > 0) {
+                for (int c = 0; c < k; ++c) v = fma(-__ldcg(a.J + (int64_t)c * a.N + i), h2n[c], v);
                 __stcg(e + i, v);
-                nacc = fma(v, v, nacc);
             }
-            if (pass == 1) {
-                nacc = warp_sum(nacc);
-                if (lane == 0) s_part[warp] = nacc;
+            n2 = fma(v, v, n2);
+            if (e2) cr = fma(v, __ldcg(e2 + i), cr);
+        }
+        if (e2)
+            for (int c = warp; c < k; c += NWARP) {
+                const double* jc = a.J + (int64_t)c * a.N;
+                double acc = 0.0;
+                for (int64_t i = r0 + lane; i < r1; i += 32) acc = fma(__ldcg(jc + i), __ldcg(e2 + i), acc);
+                acc = warp_sum(acc);
+                if (lane == 0) __stcg(part(c), acc);
             }
-            __syncthreads();
-        }
-        if (k == 0) {
-            // no direction yet: the remainder is the column itself
-            double nacc = 0.0;
-            for (int64_t i = r0 + threadIdx.x; i < r1; i += NT) {
-                const double v = __ldcg(e + i);
-                nacc = fma(v, v, nacc);
-            }
-            nacc = warp_sum(nacc);
-            if (lane == 0) s_part[warp] = nacc;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < NWARP; ++w) s += s_part[w];
-            __stcg(part(a.m), s);
-        }
-        if (!grid_sync(a.bar, &s_flag)) return;
-        if (warp == 0) {
-            double s = 0.0;
-            for (int bb = lane; bb < G; bb += 32) s += __ldcg(part_of(bb, a.m));
-            s = warp_sum(s);
-            if (lane == 0) s_nu = sqrt(s);
-        }
-        ++red;
-        __syncthreads();
-        const double nu = s_nu;
-        if (!isfinite(nu)) {
-            if (threadIdx.x == 0) grid_abort(a.bar, ST_ERR_NONFINITE);
-            return;
-        }
-        if (b == 0)
-            for (int c = threadIdx.x; c < k; c += NT) a.P[c + (int64_t)j * a.m] = h[c] + h2[c];
-        if (nu > tau && nu > 0.0) {
-            const double inv = 1.0 / nu;
-            double* jk = a.J + (int64_t)k * a.N;
-            for (int64_t i = r0 + threadIdx.x; i < r1; i += NT) __stcg(jk + i, __ldcg(e + i) * inv);
-            if (b == 0 && threadIdx.x == 0) a.P[k + (int64_t)j * a.m] = nu;
-            ++k;
-        }
-        // J(:, k-1) is read next column only on this block's own rows
-        __syncthreads();
+        write_pair(n2, cr);
+        double* t = hc;
+        hc = hn;
+        hn = t;
+        t = h2c;
+        h2c = h2n;
+        h2n = t;
     }
-    if (b == 0 && threadIdx.x == 0) *a.k_out = k;
+    if (b == 0 && tid == 0) *a.k_out = k;
 }
 
 // ---------------------------------------------------------------------------
@@ -903,14 +963,14 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     int gs_blocks = 0;
     {
         int per_sm = 0;
-        size_t smem = sizeof(double) * 2 * pdim;
+        size_t smem = sizeof(double) * 4 * pdim;
         if (smem > 48 * 1024)
             ST_CUDA_TRY(cudaFuncSetAttribute(gs2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs2_kernel, NT, smem));
         gs_blocks = std::max(1, std::min(per_sm, 1)) * m->num_sms;
         gs_blocks = (int)std::min<int64_t>(gs_blocks, std::max<int64_t>(1, N / 64));
     }
-    const size_t szPart = std::max((size_t)2 * std::max(gs_blocks, 1) * (pdim + 1), (size_t)64 * Nt);
+    const size_t szPart = std::max((size_t)2 * std::max(gs_blocks, 1) * (pdim + 2), (size_t)64 * Nt);
     const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 3 * szX + (size_t)cap * rmax * 2 +
                            szPart + pdim + 9 * cap + 32;
     ST_TRY(st_grow(m, m->ws_pod, sizeof(double) * doubles + sizeof(int) * (2 * cap + 16)));
@@ -1008,7 +1068,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         void* args[] = {&g};
         ST_PROF(m, "gs2_kernel");
         ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT), args,
-                                                sizeof(double) * 2 * pdim, st));
+                                                sizeof(double) * 4 * pdim, st));
         st_count_launch();
         return ST_OK;
     };
@@ -1158,7 +1218,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
                 void* args[] = {&g};
                 ST_PROF(m, "gs2_kernel");
                 ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT),
-                                                        args, sizeof(double) * 2 * pdim, st));
+                                                        args, sizeof(double) * 4 * pdim, st));
         st_count_launch();
                 ST_CUDA_TRY(cudaMemcpyAsync(W, W2, sizeof(double) * N * r, cudaMemcpyDeviceToDevice, st));
             }
