@@ -1,10 +1,11 @@
 // FP64 SIMT GEMM, column major, batched, with a deterministic split over K.
 //
 // GB300 issues FP64 at a small fraction of its FP32 rate, so a register tile
-// of 4x4 outputs per thread and a 64x64x16 shared-memory tile already keep
-// the FP64 pipe busy; the kernel's job is to avoid redundant global traffic
-// and to expose enough tiles (split-K) for the tall-skinny products of the
-// POD, where K is the number of spatial unknowns.
+// of 2x8 outputs per thread and a 64x64x16 shared-memory tile already keep
+// the FP64 pipe busy; the kernel's job is to avoid redundant global traffic,
+// to skip the padding of edge tiles, and to expose enough tiles (split-K,
+// balanced over the SMs) for the tall-skinny products of the POD, where K is
+// the number of spatial unknowns.
 #include <algorithm>
 
 #include "internal.h"
@@ -13,16 +14,20 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
+// 64 x 64 output tile per block, 8 warps: warp w owns the 8 contiguous
+// columns 8w..8w+7 and lane l the rows l and l + 32, so a tile that is
+// partly outside the matrix drops whole warps (columns) or the second row
+// (rows) with warp-uniform branches instead of computing padding.
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(NT, 3) dgemm_kernel(int64_t M, int64_t Nc, int64_t K, int64_t kchunk,
-                                                   double alpha, const double* __restrict__ A,
-                                                   int64_t lda, int64_t sA, const double* __restrict__ B,
-                                                   int64_t ldb, int64_t sB, double beta, double* C,
-                                                   int64_t ldc, int64_t sC, int splits, double* ws) {
+                                                      double alpha, const double* __restrict__ A,
+                                                      int64_t lda, int64_t sA, const double* __restrict__ B,
+                                                      int64_t ldb, int64_t sB, double beta, double* C,
+                                                      int64_t ldc, int64_t sC, int splits, double* ws) {
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    const int lane = tid & 31, warp = tid >> 5;
     const int64_t i0 = (int64_t)blockIdx.x * BM, j0 = (int64_t)blockIdx.y * BN;
     const int bz = blockIdx.z;
     const int batch = bz / splits, split = bz % splits;
@@ -31,15 +36,14 @@ __global__ void __launch_bounds__(NT, 3) dgemm_kernel(int64_t M, int64_t Nc, int
     C += batch * sC;
     const int64_t kb = (int64_t)split * kchunk;
     const int64_t ke = K < kb + kchunk ? K : kb + kchunk;
-    const bool full = i0 + BM <= M && j0 + BN <= Nc;
-    const int64_t rx = M - i0 - tx, ry = Nc - j0 - ty;  // valid rows / columns of this thread
-    const int nx = rx <= 0 ? 0 : (int)(rx >= 49 ? 4 : (rx + 15) / 16);
-    const int ny = ry <= 0 ? 0 : (int)(ry >= 49 ? 4 : (ry + 15) / 16);
-    double acc[4][4];
+    const int64_t rem_rows = M - i0, rem_cols = Nc - j0 - 8 * warp;
+    const bool active = rem_cols > 0;     // warp has a valid column
+    const bool two_rows = rem_rows > 32;  // rows l + 32 exist in this tile
+    double acc[2][8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int x = 0; x < 2; ++x)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int y = 0; y < 8; ++y) acc[x][y] = 0.0;
 
     for (int64_t k0 = kb; k0 < ke; k0 += BK) {
         // A tile: BM x BK
@@ -67,48 +71,37 @@ __global__ void __launch_bounds__(NT, 3) dgemm_kernel(int64_t M, int64_t Nc, int
             Bs[kk][jj] = v;
         }
         __syncthreads();
-        if (full) {
+        if (active) {
+            if (two_rows) {
 #pragma unroll
-            for (int kk = 0; kk < BK; ++kk) {
-                double a[4], b[4];
+                for (int kk = 0; kk < BK; ++kk) {
+                    const double a0 = As[kk][lane], a1 = As[kk][lane + 32];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    a[t] = As[kk][tx + 16 * t];
-                    b[t] = Bs[kk][ty + 16 * t];
+                    for (int y = 0; y < 8; ++y) {
+                        const double bv = Bs[kk][8 * warp + y];
+                        acc[0][y] = fma(a0, bv, acc[0][y]);
+                        acc[1][y] = fma(a1, bv, acc[1][y]);
+                    }
                 }
+            } else {
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+                for (int kk = 0; kk < BK; ++kk) {
+                    const double a0 = As[kk][lane];
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
-            }
-        } else {
-            // edge tile: skip the products of rows / columns past the matrix
-            // (whole warps drop out where a tile is mostly padding)
-#pragma unroll
-            for (int kk = 0; kk < BK; ++kk) {
-                double a[4], b[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    a[t] = As[kk][tx + 16 * t];
-                    b[t] = Bs[kk][ty + 16 * t];
+                    for (int y = 0; y < 8; ++y) acc[0][y] = fma(a0, Bs[kk][8 * warp + y], acc[0][y]);
                 }
-#pragma unroll
-                for (int x = 0; x < 4; ++x)
-                    if (x < nx)
-#pragma unroll
-                        for (int y = 0; y < 4; ++y)
-                            if (y < ny) acc[x][y] = fma(a[x], b[y], acc[x][y]);
             }
         }
         __syncthreads();
     }
+    if (!active) return;
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-        int64_t gi = i0 + tx + 16 * x;
+    for (int x = 0; x < 2; ++x) {
+        const int64_t gi = i0 + lane + 32 * x;
         if (gi >= M) continue;
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-            int64_t gj = j0 + ty + 16 * y;
+        for (int y = 0; y < 8; ++y) {
+            const int64_t gj = j0 + 8 * warp + y;
             if (gj >= Nc) continue;
             if (splits == 1) {
                 double* c = C + gi + gj * ldc;
@@ -183,8 +176,11 @@ st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nc,
               (unsigned)(batch * std::max(splits, 1)));
     if (grid.y > 65535 || grid.z > 65535) return st_fail(ST_ERR_ARG, "st_dgemm: grid too large");
     int sp = std::max(splits, 1);
-    ST_PROF(m, "dgemm_kernel");
-    st_prof_flops(m, "dgemm_kernel", 2.0 * (double)M * (double)Nc * (double)K * (double)batch);
+    // profile classes: tall-skinny updates (M large), split-K projections,
+    // and small products
+    const char* pname = splits > 1 ? "dgemm_kernel[split-k]" : (M >= 4096 ? "dgemm_kernel[tall]" : "dgemm_kernel[small]");
+    ST_PROF(m, pname);
+    st_prof_flops(m, pname, 2.0 * (double)M * (double)Nc * (double)K * (double)batch);
 #define ST_LAUNCH(ta, tb)                                                                   \
     dgemm_kernel<ta, tb><<<grid, NT, 0, m->stream>>>(M, Nc, K, kchunk, alpha, A, lda, sA, B, \
                                                      ldb, sB, beta, C, ldc, sC, sp, ws)

@@ -67,9 +67,11 @@ def test_profile_and_pod_stats():
     uhat = torch.zeros((3, p.ns * p.nt), dtype=torch.float64, device="cuda:0")
     m.st_rom_solve(3, dev_tensor(p.theta(p.test_mu[:3])), None, uhat)
     prof = m.st_profile_read()
-    for name in ("fom_march_kernel", "jacobi_kernel", "dgemm_kernel", "solve_kernel<double>", "gs2_kernel"):
+    for name in ("fom_march_kernel", "jacobi_kernel", "solve_kernel<double>", "gs2_kernel"):
         assert name in prof and prof[name][0] > 0.0 and prof[name][1] >= 1, name
-    assert prof["dgemm_kernel"][2] > 0 and prof["jacobi_kernel"][2] > 0
+    gemm = [v for k, v in prof.items() if k.startswith("dgemm_kernel[")]
+    assert gemm and all(v[0] > 0.0 and v[2] > 0 for v in gemm)
+    assert prof["jacobi_kernel"][2] > 0
     times = [v[0] for v in prof.values()]
     assert times == sorted(times, reverse=True)
     sweeps, reorth = m.st_pod_get_stats()
