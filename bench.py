@@ -42,6 +42,14 @@ N_FIELDS = 4
 # x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 ONLINE_REFINE = 3
+# DRAM bytes (read + write) per unit of work from ncu captures of the current
+# kernels, scaled to a launch by the units it processes (the captures and
+# their commands are summarised under profiles/)
+NCU_DRAM_BYTES = {
+    # profiles/fom_march_kernel_c4_16mu_10steps.md: 64.8 MB + 178.7 MB for 10
+    # steps of the 16-parameter march; per step of the march
+    "fom_march_kernel": {"per": "step", "bytes": (64.832768e6 + 178.686464e6) / 10},
+}
 # dependence threshold of the incremental SVD, relative to the block's largest
 # column: the value of the paper's first numerical example (Sec. 6); the
 # BiCGSTAB snapshots carry ~1e-11 relative solver error, which a smaller
@@ -504,9 +512,12 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                 k["frac_fp64"] = k["achieved_tflops"] / FP64_PEAK_TFLOPS
         kern[name] = k
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    traffic = None
+    if dom in NCU_DRAM_BYTES and NCU_DRAM_BYTES[dom]["per"] == "step":
+        traffic = NCU_DRAM_BYTES[dom]["bytes"] * Nt  # one launch marches all Nt steps
     roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom].get("achieved_tflops"),
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kern[dom].get("frac_fp64"),
-            "traffic": None, "launch_ms": kern[dom]["ms_per_step"] / kern[dom]["launches_per_step"],
+            "traffic": traffic, "launch_ms": kern[dom]["ms_per_step"] / kern[dom]["launches_per_step"],
             "peak_source": "FP64 derived: 152 SMs x 4 flop/clk x 2.07 GHz"}
     sig = np.asarray(pod_sigma)
     pod_diag = {"rank": pod_rank, "updates": len(pod_sweeps), "jacobi_sweeps": pod_sweeps,
