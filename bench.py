@@ -55,6 +55,9 @@ NCU_DRAM_BYTES = {
 # BiCGSTAB snapshots carry ~1e-11 relative solver error, which a smaller
 # threshold would take for new directions
 EPS_SVD = 2e-8
+# parameter samples per incremental-SVD update (the rank stays below r_max
+# here, so the basis is the same up to rounding for any block width)
+POD_BLOCK = 4
 
 
 def _peaks():
@@ -327,7 +330,8 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     theta_train = prob.theta(prob.train_mu)
     theta_b = prob.theta(mu_b)
     n_train = theta_train.shape[0]
-    m = st.Model(prob.rowptr, prob.col, prob.vals, st.options(r_max=args.r_max, eps_svd=EPS_SVD),
+    m = st.Model(prob.rowptr, prob.col, prob.vals,
+                 st.options(r_max=args.r_max, eps_svd=EPS_SVD, pod_block=args.pod_block),
                  stream=stream.cuda_stream)
     # online solve: FP32 LU factors with FP64 residuals and refinement, the
     # solution agrees with the FP64 LU to ~1e-16 relative (online_modes below)
@@ -538,7 +542,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                 "config": {"workload": WORKLOAD, "global_batch": world * N_BATCH, "seq_len": Nt,
                            "parallelism": f"replicas{world}", "r_max": args.r_max,
                            "online_precision": f"FP32 LU factors, FP64 residual + {ONLINE_REFINE} refinement steps",
-                           "eps_svd": EPS_SVD, "eps_sv": 1e-14,
+                           "eps_svd": EPS_SVD, "eps_sv": 1e-14, "pod_block": args.pod_block,
                            "l2": "inputs larger than L2 (1.26 GB of snapshots written per step)"},
                 "phases_ms": phases,
                 "online_solves_per_s": N_BATCH / ((phases["solve"] + phases["reconstruct"]) / 1e3),
@@ -574,7 +578,8 @@ def run_case(case: str) -> None:
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     prob = problem_for("c4")
-    m = st.Model(prob.rowptr, prob.col, prob.vals, st.options(eps_svd=EPS_SVD), stream=stream.cuda_stream)
+    m = st.Model(prob.rowptr, prob.col, prob.vals, st.options(eps_svd=EPS_SVD, pod_block=POD_BLOCK),
+                 stream=stream.cuda_stream)
     B = torch.tensor(prob.B.T.copy(), device=dev)
     n_train = len(prob.train_mu)
     if case in ("fom", "fomfull", "pod"):
@@ -652,6 +657,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--r-max", type=int, default=256)
+    ap.add_argument("--pod-block", type=int, default=POD_BLOCK, help="parameter samples per incremental-SVD update")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=200)

@@ -77,6 +77,10 @@ typedef struct {
                              with ST_ERR_TIMEOUT (one poll ~ 0.1 us)         (2e7)    */
     int32_t refine_steps; /* iterative-refinement steps of the reduced solve (1)      */
     int32_t jacobi_sweeps;/* sweep cap of the one-sided Jacobi SVD           (40)     */
+    int32_t pod_block;    /* parameter samples whose snapshots form one update
+                             of the incremental SVD (block of pod_block * Nt
+                             columns; the paper streams one sample's
+                             snapshots, 1)                                   (1)      */
 } st_options;
 
 /* Fill *opt with the defaults shown above. */

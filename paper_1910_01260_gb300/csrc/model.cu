@@ -131,6 +131,7 @@ void st_options_default(st_options* o) {
     o->spin_limit = 20000000LL;
     o->refine_steps = 1;
     o->jacobi_sweeps = 40;
+    o->pod_block = 1;
 }
 
 const char* st_last_error(void) { return g_last_error.c_str(); }
@@ -156,6 +157,7 @@ const char* st_status_string(st_status s) {
 static bool options_valid(const st_options& o) {
     return (o.tol > 0) && o.maxit >= 1 && o.r_max >= 1 && (o.eps_svd >= 0) && (o.eps_sv >= 0) &&
            o.spin_limit >= 1 && o.refine_steps >= 0 && o.refine_steps <= 16 && o.jacobi_sweeps >= 1 &&
+           o.pod_block >= 1 && o.pod_block <= 64 &&
            (o.precision == ST_FP64 || o.precision == ST_FP32_ASSEMBLY || o.precision == ST_FP32_LU);
 }
 

@@ -944,9 +944,12 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     if (n_mu > 64) return st_fail(ST_ERR_ARG, "st_rom_build_basis: at most 64 parameter samples");
     const int64_t N = m->N;
     const int rmax = (int)std::min<int64_t>(m->opt.r_max, N);
-    const int cap = rmax + Nt;
+    // one update takes the snapshots of pod_block parameter samples
+    const int pb = std::min<int>(m->opt.pod_block, n_mu);
+    const int bmax = Nt * pb;  // widest block
+    const int cap = rmax + bmax;
     const int64_t ldv = (int64_t)n_mu * Nt;
-    const int pdim = std::max(Nt, rmax);
+    const int pdim = std::max(bmax, rmax);
     cudaStream_t st = m->stream;
     st_internal_free_basis(m);
     m->pod_r = 0;
@@ -958,8 +961,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     // buffers
     ST_TRY(st_grow(m, m->W, sizeof(double) * N * cap));
     ST_TRY(st_grow(m, m->V, sizeof(double) * ldv * rmax));
-    const size_t szW2 = (size_t)N * cap, szV2 = (size_t)ldv * rmax, szE = (size_t)N * Nt,
-                 szL = (size_t)rmax * Nt, szP = (size_t)pdim * pdim, szX = (size_t)cap * cap;
+    const size_t szW2 = (size_t)N * cap, szV2 = (size_t)ldv * rmax, szE = (size_t)N * bmax,
+                 szL = (size_t)rmax * bmax, szP = (size_t)pdim * pdim, szX = (size_t)cap * cap;
     int gs_blocks = 0;
     {
         int per_sm = 0;
@@ -970,7 +973,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         gs_blocks = std::max(1, std::min(per_sm, 1)) * m->num_sms;
         gs_blocks = (int)std::min<int64_t>(gs_blocks, std::max<int64_t>(1, N / 64));
     }
-    const size_t szPart = std::max((size_t)2 * std::max(gs_blocks, 1) * (pdim + 2), (size_t)64 * Nt);
+    const size_t szPart = std::max((size_t)2 * std::max(gs_blocks, 1) * (pdim + 2), (size_t)64 * bmax);
     const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 3 * szX + (size_t)cap * rmax * 2 +
                            szPart + pdim + 9 * cap + 32;
     ST_TRY(st_grow(m, m->ws_pod, sizeof(double) * doubles + sizeof(int) * (2 * cap + 16)));
@@ -1080,24 +1083,25 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         if (herr) return st_fail(herr, "st_rom_build_basis: Gram-Schmidt failed (%s)", st_status_string(herr));
         return ST_OK;
     };
-    for (int p = 0; p < n_mu; ++p) {
-        const double* Up = snapshots + (size_t)p * Nt * N;
+    for (int p0 = 0; p0 < n_mu; p0 += pb) {
+        const int bw = Nt * std::min(pb, n_mu - p0);  // columns of this block
+        const double* Up = snapshots + (size_t)p0 * Nt * N;
         {
             const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(64, N / 2048));
             ST_PROF(m, "colnorm_kernels");
-            colnorm_part_kernel<<<dim3(Nt, chunks), NT, 0, st>>>(N, Up, chunks, partial);
+            colnorm_part_kernel<<<dim3(bw, chunks), NT, 0, st>>>(N, Up, chunks, partial);
             ST_TRY(st_check_launch("colnorm_part"));
-            colnorm_max_kernel<<<1, NT, 0, st>>>(Nt, chunks, partial, m->opt.eps_svd, d_scalar);
+            colnorm_max_kernel<<<1, NT, 0, st>>>(bw, chunks, partial, m->opt.eps_svd, d_scalar);
             ST_TRY(st_check_launch("colnorm_max"));
         }
-        ST_CUDA_TRY(cudaMemcpyAsync(E, Up, sizeof(double) * szE, cudaMemcpyDeviceToDevice, st));
+        ST_CUDA_TRY(cudaMemcpyAsync(E, Up, sizeof(double) * (size_t)N * bw, cudaMemcpyDeviceToDevice, st));
         double* J = W + (size_t)r * N;
         int k = 0;
         if (r > 0) {
             // first block pass: L = W^T U_p, E1 = U_p - W L, E1 = J1 P1
-            ST_TRY(st_dgemm(m, true, false, r, Nt, N, 1.0, W, N, Up, N, 0.0, L, rmax));
-            ST_TRY(st_dgemm(m, false, false, N, Nt, r, -1.0, W, N, L, rmax, 1.0, E, N));
-            ST_TRY(run_gs(E, Nt, J, P1, d_scalar));
+            ST_TRY(st_dgemm(m, true, false, r, bw, N, 1.0, W, N, Up, N, 0.0, L, rmax));
+            ST_TRY(st_dgemm(m, false, false, N, bw, r, -1.0, W, N, L, rmax, 1.0, E, N));
+            ST_TRY(run_gs(E, bw, J, P1, d_scalar));
             int k1 = 0;
             ST_TRY(read_k(&k1));
             if (k1 > 0) {
@@ -1124,22 +1128,22 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
                     ST_TRY(run_gs(E, k1, J, P2, nullptr));
                     ST_TRY(read_k(&k));
                 }
-                ST_TRY(st_dgemm(m, false, false, r, Nt, k1, 1.0, L2, rmax, P1, Nt, 1.0, L, rmax));
-                if (k > 0) ST_TRY(st_dgemm(m, false, false, k, Nt, k1, 1.0, P2, k1, P1, Nt, 0.0, P, Nt));
+                ST_TRY(st_dgemm(m, false, false, r, bw, k1, 1.0, L2, rmax, P1, bw, 1.0, L, rmax));
+                if (k > 0) ST_TRY(st_dgemm(m, false, false, k, bw, k1, 1.0, P2, k1, P1, bw, 0.0, P, bw));
             }
         } else {
-            ST_TRY(run_gs(E, Nt, J, P, d_scalar));
+            ST_TRY(run_gs(E, bw, J, P, d_scalar));
             ST_TRY(read_k(&k));
         }
-        const int mrows = r + Nt, ncols = r + k;
+        const int mrows = r + bw, ncols = r + k;
         if (ncols == 0) {  // nothing to add: the block is zero and W is empty
-            rows += Nt;
+            rows += bw;
             continue;
         }
         // middle matrix, transposed: X = Q^T (mrows x ncols); pivoted QR
         // X Pi = Q1 R, then one-sided Jacobi on Z = R^T with rotations
         // accumulated in Y:  Q = (Pi U_z) Sigma (Q1 Y)^T
-        build_qt_kernel<<<grid_for(m, (int64_t)mrows * ncols), 256, 0, st>>>(r, k, Nt, d_sig, L, rmax, P, Nt, X, cap);
+        build_qt_kernel<<<grid_for(m, (int64_t)mrows * ncols), 256, 0, st>>>(r, k, bw, d_sig, L, rmax, P, bw, X, cap);
         ST_TRY(st_check_launch("build_qt"));
         ST_TRY(run_qrp(mrows, ncols));
         build_rt_kernel<<<grid_for(m, (int64_t)ncols * ncols), 256, 0, st>>>(ncols, X, cap, d_piv, q_beta, Z, cap, Y, cap);
@@ -1169,7 +1173,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             if (herr) return st_fail(herr, "st_rom_build_basis: middle-matrix SVD failed (%s)", st_status_string(herr));
         }
         if (rnew == 0) {
-            rows += Nt;
+            rows += bw;
             r = 0;
             continue;
         }
@@ -1196,13 +1200,13 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         if (r > 0 && rows > 0)
             ST_TRY(st_dgemm(m, false, false, rows, rnew, r, 1.0, V, ldv, Vsel, cap, 0.0, V2, ldv));
         ST_CUDA_TRY(cudaMemcpy2DAsync(V2 + rows, sizeof(double) * ldv, Vsel + r, sizeof(double) * cap,
-                                      sizeof(double) * Nt, rnew, cudaMemcpyDeviceToDevice, st));
+                                      sizeof(double) * bw, rnew, cudaMemcpyDeviceToDevice, st));
         ST_CUDA_TRY(cudaMemcpyAsync(W, W2, sizeof(double) * N * rnew, cudaMemcpyDeviceToDevice, st));
         ST_CUDA_TRY(cudaMemcpy2DAsync(V, sizeof(double) * ldv, V2, sizeof(double) * ldv,
-                                      sizeof(double) * (rows + Nt), rnew, cudaMemcpyDeviceToDevice, st));
+                                      sizeof(double) * (rows + bw), rnew, cudaMemcpyDeviceToDevice, st));
         ST_CUDA_TRY(cudaMemcpyAsync(d_sig, d_sig_sorted, sizeof(double) * rnew, cudaMemcpyDeviceToDevice, st));
         r = rnew;
-        rows += Nt;
+        rows += bw;
         // orthogonality check of Algorithm 2 and QR re-orthogonalisation
         if (r > 1) {
             dot_kernel<<<1, NT, 0, st>>>(N, W, W + (size_t)(r - 1) * N, d_scalar + 1);

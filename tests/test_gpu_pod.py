@@ -105,3 +105,32 @@ def test_fom_and_pod_are_deterministic():
     assert np.array_equal(s0, s1)
     assert np.array_equal(g0, g1) and np.array_equal(w0, w1) and k0 == k1
     m.close()
+
+
+@pytest.mark.parametrize("pod_block", [2, 3])
+def test_pod_multi_sample_blocks(pod_block):
+    """Updates of pod_block samples' snapshots at once (the last block may be
+    shorter) against the oracle's incremental update on the same
+    concatenated blocks; temporal bases from the same V."""
+    torch = __import__("torch")
+    p = problem_for("c1")
+    blocks = oracle_fom(p, p.train_mu)
+    Nt = blocks[0].shape[1]
+    m = make_model(p, r_max=120, pod_block=pod_block)
+    sig, r = m.st_rom_build_basis(len(blocks), Nt, _snap_tensor(blocks), p.ns, p.nt)
+    W = s = V = None
+    for i in range(0, len(blocks), pod_block):
+        W, s, V = pod.incremental_update(W, s, V, np.concatenate(blocks[i:i + pod_block], axis=1), 120, 1e-12, 1e-14)
+    T, _ = pod.temporal_bases(V, len(blocks), Nt, p.ns, p.nt)
+    assert m.st_pod_get_stats()[0].__len__() == -(-len(blocks) // pod_block)
+    k = min(len(sig), len(s), 40)
+    assert np.abs(sig[:k] - s[:k]).max() < 1e-11 * s[0]
+    phi = torch.zeros((p.ns, p.N), dtype=torch.float64, device="cuda:0")
+    Tg = torch.zeros((p.ns * p.nt, Nt), dtype=torch.float64, device="cuda:0")
+    m.st_model_get_basis(phi, Tg)
+    Phi, Tm = phi.cpu().numpy().T, Tg.cpu().numpy().T
+    assert np.abs(pod.canonical_signs(Phi) - pod.canonical_signs(W[:, :p.ns])).max() < 1e-9
+    for i in range(p.ns):
+        cols = [i + p.ns * j for j in range(p.nt)]
+        assert projector_dist(Tm[:, cols], T[:, cols]) < 1e-8
+    m.close()
