@@ -158,15 +158,16 @@ def cpu_sample(prob, theta_train, mu_b, sizes, budget_steps: int = 40, n_solve: 
     fom.fom_march(A, prob.dt[:budget_steps], prob.B, prob.F[:budget_steps], None)
     t_fom = (time.perf_counter() - t0) * (Nt / budget_steps) * n_train
     # 2. POD: one incremental update on seeded blocks shaped like the
-    # workload's (a block mostly in the span of the basis plus ~40 new
-    # directions)
+    # workload's (POD_BLOCK samples' snapshots, mostly in the span of the
+    # basis plus ~40 new directions per sample)
     rng = np.random.default_rng(0)
-    b1 = rng.standard_normal((N, Nt))
-    b2 = b1 @ rng.standard_normal((Nt, Nt)) + rng.standard_normal((N, 40)) @ rng.standard_normal((40, Nt))
+    bw = Nt * POD_BLOCK
+    b1 = rng.standard_normal((N, bw))
+    b2 = b1 @ rng.standard_normal((bw, bw)) + rng.standard_normal((N, 40 * POD_BLOCK)) @ rng.standard_normal((40 * POD_BLOCK, bw))
     W, s, V = pod.incremental_update(None, None, None, b1, 256, EPS_SVD, 1e-14)
     t0 = time.perf_counter()
     pod.incremental_update(W, s, V, b2, 256, EPS_SVD, 1e-14)
-    t_pod = (time.perf_counter() - t0) * n_train
+    t_pod = (time.perf_counter() - t0) * (n_train / POD_BLOCK)
     # 3. assembly with a seeded orthonormal basis of the full size
     ns, nt = prob.ns, prob.nt
     Phi = np.linalg.qr(rng.standard_normal((N, ns)))[0]
@@ -197,7 +198,7 @@ def cpu_sample(prob, theta_train, mu_b, sizes, budget_steps: int = 40, n_solve: 
             "phases_s": {"fom": t_fom, "pod": t_pod, "assemble": t_asm, "solve": t_solve,
                          "outputs": t_out},
             "sample": (f"FOM 1 of {n_train} mu x {budget_steps} of {Nt} steps (sparse LU); "
-                       f"1 incremental-SVD update at rank 256 x {n_train}; full assembly; "
+                       f"1 incremental-SVD update of {POD_BLOCK} samples at rank 256 x {n_train // POD_BLOCK}; full assembly; "
                        f"{n_solve} of {len(mu_b)} LAPACK solves; {n_out} output evaluations; "
                        "extrapolated linearly to one full step")}
 
