@@ -34,6 +34,7 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
+constexpr int kGsPanel = 64;  // columns per Gram-Schmidt panel
 
 // ---------------------------------------------------------------------------
 // tau = eps * max_j ||U[:, j]||: block (j, c) sums column j over row chunk c
@@ -84,7 +85,8 @@ struct Gs2Args {
     int m;          // columns of E
     double* E;      // N x m (ld N), overwritten
     double* J;      // N x m (ld N) output directions
-    double* P;      // m x m (ld m), zeroed by the host
+    double* P;      // coefficients, column j at P + j * ldp, zeroed by the host
+    int ldp;
     int* k_out;
     const double* tau;  // NULL: every column adds a direction
     double* partial;    // [2 x grid x (m + 2)]
@@ -186,13 +188,13 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         // finish column j: its coefficients, and a new direction if the
         // remainder is above the threshold
         if (b == 0)
-            for (int c = tid; c < kc; c += NT) a.P[c + (int64_t)j * a.m] = hc[c] + h2c[c];
+            for (int c = tid; c < kc; c += NT) a.P[c + (int64_t)j * a.ldp] = hc[c] + h2c[c];
         const double* ej = a.E + (int64_t)j * a.N;
         if (nu > tau && nu > 0.0) {
             const double inv = 1.0 / nu;
             double* jk = a.J + (int64_t)k * a.N;
             for (int64_t i = r0 + tid; i < r1; i += NT) __stcg(jk + i, __ldcg(ej + i) * inv);
-            if (b == 0 && tid == 0) a.P[k + (int64_t)j * a.m] = nu;
+            if (b == 0 && tid == 0) a.P[k + (int64_t)j * a.ldp] = nu;
             if (tid == 0) hn[k] = s_cross * inv;
             ++k;
         }
@@ -256,6 +258,16 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         h2n = t;
     }
     if (b == 0 && tid == 0) *a.k_out = k;
+}
+
+// D(0:rows, 0:cols) += S(0:rows, 0:cols) (column major).
+__global__ void add_block_kernel(int rows, int cols, const double* __restrict__ S, int lds, double* D, int ldd) {
+    const int64_t tot = (int64_t)rows * cols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % rows), j = (int)(t / rows);
+        D[i + (int64_t)j * ldd] += S[i + (int64_t)j * lds];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -974,8 +986,9 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         gs_blocks = (int)std::min<int64_t>(gs_blocks, std::max<int64_t>(1, N / 64));
     }
     const size_t szPart = std::max((size_t)2 * std::max(gs_blocks, 1) * (pdim + 2), (size_t)64 * bmax);
+    const size_t szPan = (size_t)pdim * kGsPanel + 4 * (size_t)kGsPanel * kGsPanel;
     const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 3 * szX + (size_t)cap * rmax * 2 +
-                           szPart + pdim + 9 * cap + 32;
+                           szPart + pdim + 9 * cap + szPan + 32;
     ST_TRY(st_grow(m, m->ws_pod, sizeof(double) * doubles + sizeof(int) * (2 * cap + 16)));
     double* W2 = (double*)m->ws_pod.p;
     double* V2 = W2 + szW2;
@@ -991,7 +1004,14 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     double* Ysel = Z + szX;
     double* Vsel = Ysel + (size_t)cap * rmax;
     double* partial = Vsel + (size_t)cap * rmax;
-    double* q_beta = partial + szPart;   // [cap] R diagonal of the pivoted QR
+    // Gram-Schmidt panel workspace: H [pdim x panel] projections of a panel
+    // on the earlier directions, G, R, Rinv, Pt [panel x panel]
+    double* gsH = partial + szPart;
+    double* gsG = gsH + (size_t)pdim * kGsPanel;
+    double* gsR = gsG + (size_t)kGsPanel * kGsPanel;
+    double* gsRi = gsR + (size_t)kGsPanel * kGsPanel;
+    double* gsPt = gsRi + (size_t)kGsPanel * kGsPanel;
+    double* q_beta = partial + szPart + szPan;  // [cap] R diagonal of the pivoted QR
     double* q_tau = q_beta + cap;        // [cap] Householder coefficients
     double* q_scale = q_tau + cap;       // [cap] 1 / (x_k - beta_k)
     double* q_nrm = q_scale + cap;       // [2 cap] QR trailing norms (double buffered), then the Jacobi sweep-start norms
@@ -1064,23 +1084,80 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     int r = 0;
     int64_t rows = 0;
     std::vector<double> h_sig;
-    auto run_gs = [&](double* Ein, int mcols, double* Jout, double* Pout, const double* tau) -> st_status {
-        ST_CUDA_TRY(cudaMemsetAsync(Pout, 0, sizeof(double) * (size_t)mcols * mcols, st));
-        ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
-        Gs2Args g{N, mcols, Ein, Jout, Pout, d_int, tau, partial, bar};
-        void* args[] = {&g};
-        ST_PROF(m, "gs2_kernel");
-        ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT), args,
-                                                sizeof(double) * 4 * pdim, st));
-        st_count_launch();
-        return ST_OK;
-    };
     auto read_k = [&](int* out) -> st_status {
         ST_CUDA_TRY(cudaMemcpyAsync(out, d_int, sizeof(int), cudaMemcpyDeviceToHost, st));
         ST_CUDA_TRY(cudaStreamSynchronize(st));
         int32_t herr = 0;
         ST_CUDA_TRY(cudaMemcpy(&herr, m->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
         if (herr) return st_fail(herr, "st_rom_build_basis: Gram-Schmidt failed (%s)", st_status_string(herr));
+        return ST_OK;
+    };
+    // E (N x mcols) = J P with the column-wise CGS2 semantics (a column adds
+    // a direction when its remainder exceeds tau), by panels of kGsPanel
+    // columns.  A panel is projected twice on the directions J0 found before
+    // it with GEMMs, then the cooperative kernel orthogonalises its columns
+    // among themselves.  A direction normalised from a small remainder
+    // carries rounding along J0 amplified by the normalisation, so the
+    // panel's new directions Jn are projected on J0 once more (H3 = J0^T Jn,
+    // Jn -= J0 H3) and re-orthonormalised by Cholesky QR (Jn = Jn' R):
+    // E_panel = J0 (P0 + H3 Pn) + Jn' (R Pn).  P: column j at Pout + j * ldp;
+    // *k_total receives the number of directions.
+    auto gs_block = [&](double* Ein, int mcols, double* Jout, double* Pout, int ldp, const double* tau,
+                        int* k_total) -> st_status {
+        ST_CUDA_TRY(cudaMemsetAsync(Pout, 0, sizeof(double) * (size_t)ldp * mcols, st));
+        ST_CUDA_TRY(cudaMemsetAsync(d_int + 7, 0, sizeof(int), st));
+        int k = 0;
+        for (int c0 = 0; c0 < mcols; c0 += kGsPanel) {
+            const int pw = std::min(kGsPanel, mcols - c0);
+            double* Ep = Ein + (size_t)c0 * N;
+            double* Pp = Pout + (size_t)c0 * ldp;
+            if (k > 0) {
+                ST_TRY(st_dgemm(m, true, false, k, pw, N, 1.0, Jout, N, Ep, N, 0.0, Pp, ldp));
+                ST_TRY(st_dgemm(m, false, false, N, pw, k, -1.0, Jout, N, Pp, ldp, 1.0, Ep, N));
+                ST_TRY(st_dgemm(m, true, false, k, pw, N, 1.0, Jout, N, Ep, N, 0.0, gsH, k));
+                ST_TRY(st_dgemm(m, false, false, N, pw, k, -1.0, Jout, N, gsH, k, 1.0, Ep, N));
+                add_block_kernel<<<grid_for(m, (int64_t)k * pw), 256, 0, st>>>(k, pw, gsH, k, Pp, ldp);
+                ST_TRY(st_check_launch("add_block"));
+            }
+            ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
+            double* Jn = Jout + (size_t)k * N;
+            Gs2Args g{N, pw, Ep, Jn, Pp + k, ldp, d_int, tau, partial, bar};
+            void* args[] = {&g};
+            {
+                ST_PROF(m, "gs2_kernel");
+                ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT), args,
+                                                        sizeof(double) * 4 * kGsPanel, st));
+                st_count_launch();
+            }
+            int kp = 0;
+            ST_TRY(read_k(&kp));
+            if (k > 0 && kp > 0) {
+                // Jn -= J0 (J0^T Jn); Jn = Jn' R; P0 += H3 Pn; Pn = R Pn
+                ST_TRY(st_dgemm(m, true, false, k, kp, N, 1.0, Jout, N, Jn, N, 0.0, gsH, k));
+                ST_TRY(st_dgemm(m, false, false, N, kp, k, -1.0, Jout, N, gsH, k, 1.0, Jn, N));
+                ST_TRY(st_dgemm(m, true, false, kp, kp, N, 1.0, Jn, N, Jn, N, 0.0, gsG, kp));
+                {
+                    ST_PROF(m, "chol_inv_kernel");
+                    chol_inv_kernel<<<1, NT, 0, st>>>(kp, gsG, gsR, kGsPanel, gsRi, d_int + 7);
+                    ST_TRY(st_check_launch("chol_inv panel"));
+                }
+                ST_TRY(st_dgemm(m, false, false, N, kp, kp, 1.0, Jn, N, gsRi, kp, 0.0, Ep, N));
+                ST_CUDA_TRY(cudaMemcpyAsync(Jn, Ep, sizeof(double) * (size_t)N * kp, cudaMemcpyDeviceToDevice, st));
+                ST_TRY(st_dgemm(m, false, false, k, pw, kp, 1.0, gsH, k, Pp + k, ldp, 1.0, Pp, ldp));
+                ST_TRY(st_dgemm(m, false, false, kp, pw, kp, 1.0, gsR, kGsPanel, Pp + k, ldp, 0.0, gsPt, kGsPanel));
+                ST_CUDA_TRY(cudaMemcpy2DAsync(Pp + k, sizeof(double) * ldp, gsPt, sizeof(double) * kGsPanel,
+                                              sizeof(double) * kp, pw, cudaMemcpyDeviceToDevice, st));
+            }
+            k += kp;
+        }
+        if (k > 0) {
+            int fail = 0;
+            ST_CUDA_TRY(cudaMemcpyAsync(&fail, d_int + 7, sizeof(int), cudaMemcpyDeviceToHost, st));
+            ST_CUDA_TRY(cudaStreamSynchronize(st));
+            if (fail)
+                return st_fail(ST_ERR_BREAKDOWN, "st_rom_build_basis: panel re-orthonormalisation failed");
+        }
+        *k_total = k;
         return ST_OK;
     };
     for (int p0 = 0; p0 < n_mu; p0 += pb) {
@@ -1101,9 +1178,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             // first block pass: L = W^T U_p, E1 = U_p - W L, E1 = J1 P1
             ST_TRY(st_dgemm(m, true, false, r, bw, N, 1.0, W, N, Up, N, 0.0, L, rmax));
             ST_TRY(st_dgemm(m, false, false, N, bw, r, -1.0, W, N, L, rmax, 1.0, E, N));
-            ST_TRY(run_gs(E, bw, J, P1, d_scalar));
             int k1 = 0;
-            ST_TRY(read_k(&k1));
+            ST_TRY(gs_block(E, bw, J, P1, bw, d_scalar, &k1));
             if (k1 > 0) {
                 // second block pass: L2 = W^T J1, E2 = J1 - W L2 = J P2 by Cholesky QR
                 // (E2 is orthonormal up to the rounding carried along W, so its
@@ -1125,15 +1201,13 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
                     ST_TRY(st_dgemm(m, false, false, N, k1, k1, 1.0, E, N, X, k1, 0.0, J, N));
                     k = k1;
                 } else {
-                    ST_TRY(run_gs(E, k1, J, P2, nullptr));
-                    ST_TRY(read_k(&k));
+                    ST_TRY(gs_block(E, k1, J, P2, k1, nullptr, &k));
                 }
                 ST_TRY(st_dgemm(m, false, false, r, bw, k1, 1.0, L2, rmax, P1, bw, 1.0, L, rmax));
                 if (k > 0) ST_TRY(st_dgemm(m, false, false, k, bw, k1, 1.0, P2, k1, P1, bw, 0.0, P, bw));
             }
         } else {
-            ST_TRY(run_gs(E, bw, J, P, d_scalar));
-            ST_TRY(read_k(&k));
+            ST_TRY(gs_block(E, bw, J, P, bw, d_scalar, &k));
         }
         const int mrows = r + bw, ncols = r + k;
         if (ncols == 0) {  // nothing to add: the block is zero and W is empty
@@ -1218,7 +1292,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
                 ++m->pod_reorth;
                 ST_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)r * r, st));
                 ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
-                Gs2Args g{N, r, W, W2, P, d_int, nullptr, partial, bar};
+                Gs2Args g{N, r, W, W2, P, r, d_int, nullptr, partial, bar};
                 void* args[] = {&g};
                 ST_PROF(m, "gs2_kernel");
                 ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT),
