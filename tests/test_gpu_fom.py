@@ -123,3 +123,42 @@ def test_fom_deterministic():
     b, _, _ = gpu_fom(m, p, p.train_mu)
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
     m.close()
+
+
+def test_fom_term_split_random_affine_operator():
+    """A random 3-term affine operator whose entries have one, two or three
+    nonzero terms (and some explicit all-zero entries): the march's
+    term-split operator (shared single-term values scaled by theta_q, per
+    sample values where terms overlap) against the oracle's CSR."""
+    import types
+    rng = np.random.default_rng(11)
+    N, Q, Nt = 300, 3, 8
+    rows, cols = [], []
+    for r in range(N):
+        nb = rng.choice(N, size=7, replace=False)
+        cs = np.unique(np.concatenate([[r], nb]))
+        rows += [r] * len(cs)
+        cols += list(cs)
+    rows, cols = np.array(rows), np.array(cols)
+    nnz = len(rows)
+    mask = rng.random((Q, nnz)) < 0.5
+    mask[:, rows == cols] = True                       # diagonal in every term
+    mask[:, rng.random(nnz) < 0.05] = False            # explicit all-zero entries
+    vals = rng.standard_normal((Q, nnz)) * mask * 0.3
+    diag = rows == cols
+    vals[:, diag] = -np.abs(vals[:, diag]) - 2.0       # dissipative diagonal
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=N))]).astype(np.int64)
+    Bm = rng.standard_normal((N, 1))
+    dt = np.full(Nt, 0.05)
+    F = np.sin(np.arange(1, Nt + 1) * 0.3)[:, None]
+    p = types.SimpleNamespace(N=N, rowptr=rowptr, col=cols.astype(np.int32), vals=vals, B=Bm, F=F, dt=dt,
+                              Nt=Nt, theta=lambda t: np.asarray(t, dtype=np.float64))
+    thetas = np.array([[1.0, 0.7, 0.3], [1.0, 1.3, 0.9], [0.5, 0.2, 1.1]])
+    m = make_model(p)
+    got, status, _ = gpu_fom(m, p, thetas)
+    assert (status == 0).all()
+    for k, th in enumerate(thetas):
+        A = fom.affine_operator(p.rowptr, p.col, p.vals, th)
+        ref = fom.fom_march(A, dt, Bm, F, None)
+        assert rel_max(got[k], ref) < TOL
+    m.close()
