@@ -67,6 +67,15 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
 
 
+def bench_config(args, world: int, Nt: int) -> dict:
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": WORKLOAD, "global_batch": world * N_BATCH, "seq_len": Nt,
+            "parallelism": f"replicas{world}", "r_max": args.r_max,
+            "online_precision": f"FP32 LU factors, FP64 residual + {ONLINE_REFINE} refinement steps",
+            "eps_svd": EPS_SVD, "eps_sv": 1e-14, "pod_block": args.pod_block,
+            "l2": "inputs larger than L2 (1.26 GB of snapshots written per step)"}
+
+
 def aggregate(local_ms: float, units_per_rank: int, dist, device=None):
     """Max-over-ranks step time and the whole-job throughput (units of all
     ranks / that time).  Replicas: every rank processes its own units and
@@ -157,17 +166,17 @@ def cpu_sample(prob, theta_train, mu_b, sizes, budget_steps: int = 40, n_solve: 
     t0 = time.perf_counter()
     fom.fom_march(A, prob.dt[:budget_steps], prob.B, prob.F[:budget_steps], None)
     t_fom = (time.perf_counter() - t0) * (Nt / budget_steps) * n_train
-    # 2. POD: one incremental update on seeded blocks shaped like the
-    # workload's (POD_BLOCK samples' snapshots, mostly in the span of the
-    # basis plus ~40 new directions per sample)
+    # 2. POD: one incremental update of one sample's snapshots on seeded
+    # blocks shaped like the workload's (mostly in the span of the basis
+    # plus ~40 new directions), times the 16 samples (the wider blocks of
+    # the GPU run would take the oracle longer per column)
     rng = np.random.default_rng(0)
-    bw = Nt * POD_BLOCK
-    b1 = rng.standard_normal((N, bw))
-    b2 = b1 @ rng.standard_normal((bw, bw)) + rng.standard_normal((N, 40 * POD_BLOCK)) @ rng.standard_normal((40 * POD_BLOCK, bw))
+    b1 = rng.standard_normal((N, Nt))
+    b2 = b1 @ rng.standard_normal((Nt, Nt)) + rng.standard_normal((N, 40)) @ rng.standard_normal((40, Nt))
     W, s, V = pod.incremental_update(None, None, None, b1, 256, EPS_SVD, 1e-14)
     t0 = time.perf_counter()
     pod.incremental_update(W, s, V, b2, 256, EPS_SVD, 1e-14)
-    t_pod = (time.perf_counter() - t0) * (n_train / POD_BLOCK)
+    t_pod = (time.perf_counter() - t0) * n_train
     # 3. assembly with a seeded orthonormal basis of the full size
     ns, nt = prob.ns, prob.nt
     Phi = np.linalg.qr(rng.standard_normal((N, ns)))[0]
@@ -198,7 +207,7 @@ def cpu_sample(prob, theta_train, mu_b, sizes, budget_steps: int = 40, n_solve: 
             "phases_s": {"fom": t_fom, "pod": t_pod, "assemble": t_asm, "solve": t_solve,
                          "outputs": t_out},
             "sample": (f"FOM 1 of {n_train} mu x {budget_steps} of {Nt} steps (sparse LU); "
-                       f"1 incremental-SVD update of {POD_BLOCK} samples at rank 256 x {n_train // POD_BLOCK}; full assembly; "
+                       f"1 incremental-SVD update of one sample's block x {n_train}; full assembly; "
                        f"{n_solve} of {len(mu_b)} LAPACK solves; {n_out} output evaluations; "
                        "extrapolated linearly to one full step")}
 
@@ -222,8 +231,7 @@ def run_reference(args, rank: int, world: int) -> None:
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * N_BATCH / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": N_BATCH, "seq_len": prob.Nt,
-                       "parallelism": "replicas"},
+            "config": bench_config(args, 1, prob.Nt),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": samp["sample"],
                              "phases_s": samp["phases_s"]},
@@ -540,11 +548,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "global_batch": world * N_BATCH, "seq_len": Nt,
-                           "parallelism": f"replicas{world}", "r_max": args.r_max,
-                           "online_precision": f"FP32 LU factors, FP64 residual + {ONLINE_REFINE} refinement steps",
-                           "eps_svd": EPS_SVD, "eps_sv": 1e-14, "pod_block": args.pod_block,
-                           "l2": "inputs larger than L2 (1.26 GB of snapshots written per step)"},
+                "config": bench_config(args, world, Nt),
                 "phases_ms": phases,
                 "online_solves_per_s": N_BATCH / ((phases["solve"] + phases["reconstruct"]) / 1e3),
                 "online_modes": online,
