@@ -52,6 +52,14 @@ typedef int32_t st_status;
 #define ST_FP32_ASSEMBLY 1  /* FP32 assembly of Ahat^st, FP64 LU + FP64 refinement     */
 #define ST_FP32_LU       2  /* FP32 assembly and LU factors, FP64 residual refinement   */
 
+/* Arithmetic of the FP64 products of the basis construction and assembly
+ * (st_options.fp64_gemm). */
+#define ST_DGEMM_SIMT   0  /* FP64 multiply-adds on the SIMT cores                   */
+#define ST_DGEMM_OZAKI  1  /* BF16 tensor cores on exact 8-digit operand splits
+                              (Ozaki et al., Numer. Algorithms 59, 2012): FP64-
+                              accurate, deterministic; used for products of at
+                              least 2^20 flops with K >= 8                       */
+
 /* Opaque model handle: operator terms, bases, reduced operators, workspace. */
 typedef struct st_model st_model;
 
@@ -81,6 +89,7 @@ typedef struct {
                              of the incremental SVD (block of pod_block * Nt
                              columns; the paper streams one sample's
                              snapshots, 1)                                   (1)      */
+    int32_t fp64_gemm;    /* ST_DGEMM_SIMT or ST_DGEMM_OZAKI            (ST_DGEMM_OZAKI)  */
 } st_options;
 
 /* Fill *opt with the defaults shown above. */
@@ -201,6 +210,21 @@ st_status st_profile_read(st_model* m, int32_t cap, char* names, double* ms, int
  * re-orthogonalised W in *n_reorth (may be NULL). */
 st_status st_pod_get_stats(st_model* m, int32_t* n_updates, int32_t* sweeps, int32_t cap,
                            int32_t* n_reorth);
+
+/* The FP64 matrix product of the incremental SVD and of the assembly
+ * (Sec. 4.2: projections of snapshot blocks on the basis, W^T U and
+ * U - W (W^T U), and the basis rotation), on the model's stream with the
+ * model's options.fp64_gemm:
+ *     C = alpha op(A) op(B) + beta C,  op(A) M x K, op(B) K x N, C M x N,
+ * column major; op(X) = X^T when trans_X is nonzero.  A, B, C are DEVICE
+ * pointers with leading dimensions lda >= rows of A as stored, etc.; C must
+ * not overlap A or B.  K = 0 scales C by beta.  Asynchronous: ST_ERR_ARG for
+ * a NULL model or negative sizes; device-side NaN/Inf in an operand of the
+ * tensor-core path is reported as ST_ERR_NONFINITE by a later
+ * synchronising call. */
+st_status st_gemm_f64(st_model* m, int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K,
+                      double alpha, const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                      double* C, int64_t ldc);
 
 /* Offline assembly of the space-time reduced operators through the block
  * structure of Sec. 4.3, never forming Phi_st:

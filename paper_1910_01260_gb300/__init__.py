@@ -5,6 +5,8 @@ from .binding import (  # noqa: F401
     LIB_PATH,
     Model,
     StError,
+    ST_DGEMM_OZAKI,
+    ST_DGEMM_SIMT,
     ST_ERR_ARG,
     ST_ERR_BREAKDOWN,
     ST_ERR_NONFINITE,

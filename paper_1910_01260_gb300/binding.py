@@ -31,6 +31,8 @@ ST_ERR_STATE = 9
 ST_FP64 = 0
 ST_FP32_ASSEMBLY = 1
 ST_FP32_LU = 2
+ST_DGEMM_SIMT = 0
+ST_DGEMM_OZAKI = 1
 PROFILE_NAME_LEN = 64
 
 
@@ -44,7 +46,7 @@ class st_options(ctypes.Structure):
     _fields_ = [("tol", c_double), ("maxit", c_int32), ("eps_svd", c_double),
                 ("eps_sv", c_double), ("r_max", c_int32), ("precision", c_int32),
                 ("spin_limit", c_int64), ("refine_steps", c_int32), ("jacobi_sweeps", c_int32),
-                ("pod_block", c_int32)]
+                ("pod_block", c_int32), ("fp64_gemm", c_int32)]
 
 
 class st_affine_csr(ctypes.Structure):
@@ -75,6 +77,8 @@ _SIGS = {
     "st_pod_get_stats": (c_int32, [_P, _P, _P, c_int32, _P]),
     "st_profile_enable": (c_int32, [_P, c_int32]),
     "st_profile_read": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
+    "st_gemm_f64": (c_int32, [_P, c_int32, c_int32, c_int64, c_int64, c_int64, c_double, _P, c_int64, _P,
+                              c_int64, c_double, _P, c_int64]),
     "st_rom_assemble": (c_int32, [_P, _P, c_int32, _P, _P, _P]),
     "st_model_get_reduced": (c_int32, [_P, _P, _P, _P, _P, _P]),
     "st_rom_solve": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
@@ -236,6 +240,10 @@ class Model:
             name = bytes(names[i]).split(b"\0", 1)[0].decode()
             out[name] = (float(ms[i]), int(cnt[i]), float(fl[i]))
         return out
+
+    def st_gemm_f64(self, trans_a, trans_b, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc) -> None:
+        check(lib.st_gemm_f64(self.handle, int(trans_a), int(trans_b), M, N, K, alpha, ptr(A), lda, ptr(B), ldb,
+                              beta, ptr(C), ldc))
 
     def st_rom_assemble(self, dt, B, F, u0=None) -> None:
         dth = _host(dt, np.float64)

@@ -128,11 +128,26 @@ __global__ void splitk_reduce(int64_t M, int64_t Nc, int splits, const double* _
 
 }  // namespace
 
+static bool use_ozaki(const st_model* m, int64_t M, int64_t Nc, int64_t K) {
+    return m->opt.fp64_gemm == ST_DGEMM_OZAKI && K >= 8 && 2.0 * (double)M * (double)Nc * (double)K >= 1048576.0;
+}
+
+st_status st_dgemm_slot(st_model* m, int slotA, bool reuseA, bool transA, bool transB, int64_t M, int64_t Nc,
+                        int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                        double beta, double* C, int64_t ldc) {
+    if (M > 0 && Nc > 0 && use_ozaki(m, M, Nc, K))
+        return st_ozaki_gemm(m, transA, transB, M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc, slotA, reuseA);
+    return st_dgemm(m, transA, transB, M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
 st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nc, int64_t K,
                    double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                    double beta, double* C, int64_t ldc, int batch, int64_t sA, int64_t sB,
                    int64_t sC) {
     if (M <= 0 || Nc <= 0 || batch <= 0) return ST_OK;
+    // large products go to the tensor cores (exact operand splitting)
+    if (batch == 1 && use_ozaki(m, M, Nc, K))
+        return st_ozaki_gemm(m, transA, transB, M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc);
     if (K <= 0) {
         // C = beta * C
         if (beta == 1.0) return ST_OK;
@@ -196,4 +211,17 @@ st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nc,
         ST_TRY(st_check_launch("splitk_reduce"));
     }
     return ST_OK;
+}
+
+extern "C" st_status st_gemm_f64(st_model* m, int32_t trans_a, int32_t trans_b, int64_t M, int64_t N, int64_t K,
+                                 double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                                 double beta, double* C, int64_t ldc) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_gemm_f64: NULL model");
+    if (M < 0 || N < 0 || K < 0) return st_fail(ST_ERR_ARG, "st_gemm_f64: negative size");
+    if (M == 0 || N == 0) return ST_OK;
+    if (!C || (K > 0 && (!A || !B))) return st_fail(ST_ERR_ARG, "st_gemm_f64: NULL operand");
+    const int64_t rowsA = trans_a ? K : M, rowsB = trans_b ? N : K;
+    if (lda < std::max<int64_t>(1, rowsA) || ldb < std::max<int64_t>(1, rowsB) || ldc < M)
+        return st_fail(ST_ERR_ARG, "st_gemm_f64: leading dimension too small");
+    return st_dgemm(m, trans_a != 0, trans_b != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }

@@ -37,6 +37,17 @@ struct ProfState {
     std::vector<double> flops;
 };
 
+// Digit planes of one operand of the tensor-core FP64 GEMM kept across calls
+// (the basis W and the block's directions J of the incremental SVD), with the
+// key of the matrix they were made from.
+struct OzSlot {
+    DevBuf planes, exps;
+    const double* src = nullptr;
+    int64_t ld = 0, rows = 0, K = 0;
+    bool transposed = false, valid = false;
+};
+constexpr int kOzSlots = 4;
+
 struct st_model {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -98,7 +109,8 @@ struct st_model {
     unsigned int* d_bar = nullptr;  // [4]: arrival count, generation, abort flag, queue head
 
     // scratch buffers (grown on demand, reused across calls)
-    DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_solve, ws_misc;
+    DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_oz, ws_solve, ws_misc;
+    OzSlot oz_slot[kOzSlots];
 
     // learned surrogate mu -> uhat (3-layer MLP, FP32 masters, BF16 copies)
     struct Mlp {
@@ -168,6 +180,24 @@ st_status st_dgemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Nco
                    double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                    double beta, double* C, int64_t ldc, int batch = 1, int64_t sA = 0,
                    int64_t sB = 0, int64_t sC = 0);
+
+// The same product on the BF16 tensor cores by exact operand splitting (batch
+// 1; FP64-accurate, deterministic).  st_dgemm routes its large products here
+// when options.fp64_gemm is ST_DGEMM_OZAKI.  With slotA >= 0 the digit planes
+// of op(A) are kept in m->oz_slot[slotA]; reuseA = true asserts that A has not
+// changed since that slot was filled from the same matrix (same pointer,
+// leading dimension, shape and transposition), so its planes are used as
+// they are.
+st_status st_ozaki_gemm(st_model* m, bool transA, bool transB, int64_t M, int64_t Ncols, int64_t K, double alpha,
+                        const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                        int64_t ldc, int slotA = -1, bool reuseA = false);
+// st_dgemm with the operand-plane cache of the tensor-core path (ignored on
+// the SIMT path).
+st_status st_dgemm_slot(st_model* m, int slotA, bool reuseA, bool transA, bool transB, int64_t M, int64_t Ncols,
+                        int64_t K, double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                        double beta, double* C, int64_t ldc);
+// Forget every cached operand (the matrices they came from may change).
+void st_oz_invalidate(st_model* m);
 
 // Release basis (and reduced operators) / reduced operators only.
 void st_internal_free_basis(st_model* m);

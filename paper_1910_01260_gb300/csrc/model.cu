@@ -132,6 +132,7 @@ void st_options_default(st_options* o) {
     o->refine_steps = 1;
     o->jacobi_sweeps = 40;
     o->pod_block = 1;
+    o->fp64_gemm = ST_DGEMM_OZAKI;
 }
 
 const char* st_last_error(void) { return g_last_error.c_str(); }
@@ -158,6 +159,7 @@ static bool options_valid(const st_options& o) {
     return (o.tol > 0) && o.maxit >= 1 && o.r_max >= 1 && (o.eps_svd >= 0) && (o.eps_sv >= 0) &&
            o.spin_limit >= 1 && o.refine_steps >= 0 && o.refine_steps <= 16 && o.jacobi_sweeps >= 1 &&
            o.pod_block >= 1 && o.pod_block <= 64 &&
+           (o.fp64_gemm == ST_DGEMM_SIMT || o.fp64_gemm == ST_DGEMM_OZAKI) &&
            (o.precision == ST_FP64 || o.precision == ST_FP32_ASSEMBLY || o.precision == ST_FP32_LU);
 }
 
@@ -250,11 +252,15 @@ void st_model_destroy(st_model* m) {
     cudaFree(m->d_tq_val);
     cudaFree(m->d_err);
     cudaFree(m->d_bar);
-    for (DevBuf* b : {&m->W, &m->V, &m->ws_fom, &m->ws_pod, &m->ws_pod2, &m->ws_gemm,
+    for (DevBuf* b : {&m->W, &m->V, &m->ws_fom, &m->ws_pod, &m->ws_pod2, &m->ws_gemm, &m->ws_oz,
                       &m->ws_solve, &m->ws_misc, &m->mlp.params, &m->mlp.grad, &m->mlp.adam_m,
                       &m->mlp.adam_v, &m->mlp.wbf, &m->mlp.stats, &m->mlp.act, &m->mlp.kall,
                       &m->mlp.list})
         cudaFree(b->p);
+    for (OzSlot& sl : m->oz_slot) {
+        cudaFree(sl.planes.p);
+        cudaFree(sl.exps.p);
+    }
     cudaSetDevice(cur);
     delete m;
 }

@@ -969,6 +969,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     m->sigma.clear();
     m->pod_sweeps.clear();
     m->pod_reorth = 0;
+    st_oz_invalidate(m);
 
     // buffers
     ST_TRY(st_grow(m, m->W, sizeof(double) * N * cap));
@@ -1112,10 +1113,12 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             double* Ep = Ein + (size_t)c0 * N;
             double* Pp = Pout + (size_t)c0 * ldp;
             if (k > 0) {
-                ST_TRY(st_dgemm(m, true, false, k, pw, N, 1.0, Jout, N, Ep, N, 0.0, Pp, ldp));
-                ST_TRY(st_dgemm(m, false, false, N, pw, k, -1.0, Jout, N, Pp, ldp, 1.0, Ep, N));
-                ST_TRY(st_dgemm(m, true, false, k, pw, N, 1.0, Jout, N, Ep, N, 0.0, gsH, k));
-                ST_TRY(st_dgemm(m, false, false, N, pw, k, -1.0, Jout, N, gsH, k, 1.0, Ep, N));
+                // J0 is the same matrix in all four products: its digit
+                // planes (tensor-core path) are made once per layout
+                ST_TRY(st_dgemm_slot(m, 0, false, true, false, k, pw, N, 1.0, Jout, N, Ep, N, 0.0, Pp, ldp));
+                ST_TRY(st_dgemm_slot(m, 1, false, false, false, N, pw, k, -1.0, Jout, N, Pp, ldp, 1.0, Ep, N));
+                ST_TRY(st_dgemm_slot(m, 0, true, true, false, k, pw, N, 1.0, Jout, N, Ep, N, 0.0, gsH, k));
+                ST_TRY(st_dgemm_slot(m, 1, true, false, false, N, pw, k, -1.0, Jout, N, gsH, k, 1.0, Ep, N));
                 add_block_kernel<<<grid_for(m, (int64_t)k * pw), 256, 0, st>>>(k, pw, gsH, k, Pp, ldp);
                 ST_TRY(st_check_launch("add_block"));
             }
@@ -1133,8 +1136,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             ST_TRY(read_k(&kp));
             if (k > 0 && kp > 0) {
                 // Jn -= J0 (J0^T Jn); Jn = Jn' R; P0 += H3 Pn; Pn = R Pn
-                ST_TRY(st_dgemm(m, true, false, k, kp, N, 1.0, Jout, N, Jn, N, 0.0, gsH, k));
-                ST_TRY(st_dgemm(m, false, false, N, kp, k, -1.0, Jout, N, gsH, k, 1.0, Jn, N));
+                ST_TRY(st_dgemm_slot(m, 0, true, true, false, k, kp, N, 1.0, Jout, N, Jn, N, 0.0, gsH, k));
+                ST_TRY(st_dgemm_slot(m, 1, true, false, false, N, kp, k, -1.0, Jout, N, gsH, k, 1.0, Jn, N));
                 ST_TRY(st_dgemm(m, true, false, kp, kp, N, 1.0, Jn, N, Jn, N, 0.0, gsG, kp));
                 {
                     ST_PROF(m, "chol_inv_kernel");
@@ -1176,17 +1179,17 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         int k = 0;
         if (r > 0) {
             // first block pass: L = W^T U_p, E1 = U_p - W L, E1 = J1 P1
-            ST_TRY(st_dgemm(m, true, false, r, bw, N, 1.0, W, N, Up, N, 0.0, L, rmax));
-            ST_TRY(st_dgemm(m, false, false, N, bw, r, -1.0, W, N, L, rmax, 1.0, E, N));
+            ST_TRY(st_dgemm_slot(m, 2, false, true, false, r, bw, N, 1.0, W, N, Up, N, 0.0, L, rmax));
+            ST_TRY(st_dgemm_slot(m, 3, false, false, false, N, bw, r, -1.0, W, N, L, rmax, 1.0, E, N));
             int k1 = 0;
             ST_TRY(gs_block(E, bw, J, P1, bw, d_scalar, &k1));
             if (k1 > 0) {
                 // second block pass: L2 = W^T J1, E2 = J1 - W L2 = J P2 by Cholesky QR
                 // (E2 is orthonormal up to the rounding carried along W, so its
                 // Gram matrix is well conditioned); L += L2 P1, P = P2 P1
-                ST_TRY(st_dgemm(m, true, false, r, k1, N, 1.0, W, N, J, N, 0.0, L2, rmax));
+                ST_TRY(st_dgemm_slot(m, 2, true, true, false, r, k1, N, 1.0, W, N, J, N, 0.0, L2, rmax));
                 ST_CUDA_TRY(cudaMemcpyAsync(E, J, sizeof(double) * N * k1, cudaMemcpyDeviceToDevice, st));
-                ST_TRY(st_dgemm(m, false, false, N, k1, r, -1.0, W, N, L2, rmax, 1.0, E, N));
+                ST_TRY(st_dgemm_slot(m, 3, true, false, false, N, k1, r, -1.0, W, N, L2, rmax, 1.0, E, N));
                 ST_TRY(st_dgemm(m, true, false, k1, k1, N, 1.0, E, N, E, N, 0.0, Y, k1));
                 ST_CUDA_TRY(cudaMemsetAsync(d_int + 6, 0, sizeof(int), st));
                 {

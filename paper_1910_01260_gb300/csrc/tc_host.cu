@@ -42,6 +42,30 @@ st_status tmap_bf16(CUtensorMap* map, const void* base, int rows, int cols, int 
     return ST_OK;
 }
 
+}  // namespace
+
+// 3-D BF16 array depth x rows x inner (inner contiguous; row stride ld and
+// plane stride `plane` in elements, multiples of 8), tile box_inner x
+// box_rows x box_depth with the 128-byte swizzle (box_inner * 2 <= 128).
+st_status st_tmap_bf16_3d(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int64_t depth,
+                          int64_t ld, int64_t plane, int box_inner, int box_rows, int box_depth) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc;
+    ST_TRY(encoder(&enc));
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16 || (plane * 2) % 16 || box_inner * 2 > 128)
+        return st_fail(ST_ERR_ARG, "st_tmap_bf16_3d: misaligned base, strides or box");
+    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)depth};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)plane * 2};
+    cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, (cuuint32_t)box_depth};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return st_fail(ST_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed (%d)", (int)r);
+    return ST_OK;
+}
+
+namespace {
+
 template <int BN>
 st_status launch(st_model* m, int M, int N, const CUtensorMap& ta, const CUtensorMap& tb, const tc::GemmArgs& g) {
     const size_t smem = tc::smem_bytes(BN);
