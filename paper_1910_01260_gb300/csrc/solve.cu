@@ -14,6 +14,7 @@
 // a register-tiled 64x64 FP64 product), solves, refines with an FP64
 // residual regenerated from (Ahat, G, M, S) and reports ||r|| / ||rhs||.
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -56,41 +57,13 @@ struct Smem {
     double* r;    // residual / correction
     int* piv;     // pivots
     int* perm;    // row permutation of the pivots (row i of P A is row perm[i] of A)
-    T* D;         // 2 x 32 x 32 diagonal blocks for the triangular solves
+    T* D;         // 2 x 32 x 32 diagonal blocks for the triangular solves (the
+                  // inverse of the panel's unit lower block during the factorisation)
+    int* cur;     // [nfull] panel row at each position after the panel's swaps
+    int* where;   // [nfull] position of each panel row
+    int* pl;      // [2 x 2 nb] moved rows of a panel step: destination, source
+    int* pp;      // [nb] pivot rows of the panel (panel-relative, rows kept in place)
 };
-
-__device__ __forceinline__ void block_argmax(double v, int idx, double* s_val, int* s_idx,
-                                             double& out_v, int& out_i) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (v2 > v || (v2 == v && i2 < idx)) {
-            v = v2;
-            idx = i2;
-        }
-    }
-    if (lane == 0) {
-        s_val[warp] = v;
-        s_idx[warp] = idx;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double bv = s_val[0];
-        int bi = s_idx[0];
-        for (int w = 1; w < NWARP; ++w)
-            if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bi)) {
-                bv = s_val[w];
-                bi = s_idx[w];
-            }
-        s_val[0] = bv;
-        s_idx[0] = bi;
-    }
-    __syncthreads();
-    out_v = s_val[0];
-    out_i = s_idx[0];
-}
 
 __device__ __forceinline__ double block_sum(double v, double* s_val) {
     v = warp_sum(v);
@@ -102,77 +75,199 @@ __device__ __forceinline__ double block_sum(double v, double* s_val) {
     return t;
 }
 
-// In-place LU with partial pivoting of A (n x n, ld n), in the arithmetic of
-// T.  Returns false if a zero pivot occurred (the factorisation still
-// completes, as in LAPACK).
+constexpr int kRowsPerThread = 8;  // panel rows a thread owns: nfull <= 8 * NT
+
+// Pivot candidate of a warp: largest magnitude, ties to the lower row.
 template <typename T>
-__device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, double* s_val, int* s_idx) {
+__device__ __forceinline__ void warp_argmax(T& bv, int& bi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v2 > bv || (v2 == bv && i2 < bi)) {
+            bv = v2;
+            bi = i2;
+        }
+    }
+}
+
+// Partial-pivoting LU of the rp x w panel in shared memory (ld ld_p) with its
+// rows left in place: the row chosen as pivot c is frozen (it holds row c of
+// U), the other rows are eliminated.  Thread t owns rows t, t + NT, ..., so
+// the scan for the next pivot runs over the rows the thread has just updated
+// and one block barrier per column suffices.  pp[c] receives the panel row of
+// pivot c; false on a zero pivot (the elimination still completes, as in
+// LAPACK).
+template <typename T>
+__device__ bool panel_factor(T* P, int rp, int w, int ld_p, int* pp, T (*s_cv)[NWARP], int (*s_ci)[NWARP]) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned used = 0;  // bit k: row tid + k NT is a pivot row
     bool ok = true;
-    const int tid = threadIdx.x;
+    // magnitudes are compared in T: FP64 compares would run on the slow FP64 pipe
+    auto scan = [&](int col, int buf) {
+        T bv = (T)-1;
+        int bi = INT_MAX;
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const int r = tid + k * NT;
+            if (r < rp && !((used >> k) & 1u)) {
+                const T v = fabs(P[r + col * ld_p]);
+                if (v > bv) {
+                    bv = v;
+                    bi = r;
+                }
+            }
+        }
+        warp_argmax(bv, bi);
+        if (lane == 0) {
+            s_cv[buf][warp] = bv;
+            s_ci[buf][warp] = bi;
+        }
+    };
+    scan(0, 0);
+    __syncthreads();
+    for (int c = 0; c < w; ++c) {
+        const int buf = c & 1;
+        T bv = s_cv[buf][0];
+        int pr = s_ci[buf][0];
+        for (int q = 1; q < NWARP; ++q) {
+            const T v = s_cv[buf][q];
+            const int i = s_ci[buf][q];
+            if (v > bv || (v == bv && i < pr)) {
+                bv = v;
+                pr = i;
+            }
+        }
+        if (tid == 0) pp[c] = pr;
+        const T pv = P[pr + c * ld_p];
+        if (pv == (T)0) ok = false;
+        const T inv = pv != (T)0 ? (T)1 / pv : (T)1;  // a zero pivot column is all zero: nothing to scale
+        if (pr % NT == tid) used |= 1u << (pr / NT);
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const int r = tid + k * NT;
+            if (r < rp && !((used >> k) & 1u)) {
+                const T l = P[r + c * ld_p] * inv;
+                P[r + c * ld_p] = l;
+                for (int cc = c + 1; cc < w; ++cc) P[r + cc * ld_p] = fma(-l, P[pr + cc * ld_p], P[r + cc * ld_p]);
+            }
+        }
+        if (c + 1 < w) scan(c + 1, buf ^ 1);
+        __syncthreads();
+    }
+    return ok;
+}
+
+// In-place LU with partial pivoting of A (n x n, ld n), in the arithmetic of
+// T, right-looking in panels of nb columns: the panel is factorised in shared
+// memory with its rows in place (panel_factor), its pivots are turned into
+// the LAPACK swap sequence (piv), the moved rows of the other columns are
+// exchanged through shared memory in one gather and one scatter, U12 is
+// L11^{-1} A12 with the explicit inverse of the unit lower 32 x 32 block, and
+// A22 -= L21 U12 in register-tiled column chunks.  Returns false if a zero
+// pivot occurred (the factorisation still completes, as in LAPACK).
+template <typename T>
+__device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[NWARP], int (*s_ci)[NWARP],
+                          int* s_npl) {
+    bool ok = true;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cap = ld_p * nb;  // elements of the panel buffer, reused as staging
     for (int kb = 0; kb < n; kb += nb) {
         const int w = min(nb, n - kb), rp = n - kb;
         for (int t = tid; t < rp * w; t += NT) {
             const int r = t % rp, c = t / rp;
             s.P[r + c * ld_p] = A[(kb + r) + (int64_t)(kb + c) * n];
         }
-        __syncthreads();
-        for (int c = 0; c < w; ++c) {
-            double bv = -1.0;
-            int bi = c;
-            for (int r = c + tid; r < rp; r += NT) {
-                const double v = fabs((double)s.P[r + c * ld_p]);
-                if (v > bv) {
-                    bv = v;
-                    bi = r;
-                }
-            }
-            double mv;
-            int pr;
-            block_argmax(bv, bi, s_val, s_idx, mv, pr);
-            if (tid == 0) s.piv[kb + c] = kb + pr;
-            if (pr != c)
-                for (int cc = tid; cc < w; cc += NT) {
-                    const T t0 = s.P[c + cc * ld_p];
-                    s.P[c + cc * ld_p] = s.P[pr + cc * ld_p];
-                    s.P[pr + cc * ld_p] = t0;
-                }
-            __syncthreads();
-            const T pv = s.P[c + c * ld_p];
-            if (pv == (T)0) {
-                ok = false;
-            } else {
-                const T inv = (T)1 / pv;
-                for (int r = c + 1 + tid; r < rp; r += NT) s.P[r + c * ld_p] *= inv;
-            }
-            __syncthreads();
-            const int nr = rp - c - 1, nc = w - c - 1;
-            if (nr > 0 && nc > 0)
-                for (int t = tid; t < nr * nc; t += NT) {
-                    const int r = c + 1 + t % nr, cc = c + 1 + t / nr;
-                    s.P[r + cc * ld_p] = fma(-s.P[r + c * ld_p], s.P[c + cc * ld_p], s.P[r + cc * ld_p]);
-                }
-            __syncthreads();
+        for (int r = tid; r < rp; r += NT) {
+            s.cur[r] = r;
+            s.where[r] = r;
         }
+        __syncthreads();
+        if (!panel_factor(s.P, rp, w, ld_p, s.pp, s_cv, s_ci)) ok = false;
+        if (tid == 0) {
+            // the swap sequence that brings pivot row pp[c] to position c
+            int npl = 0;
+            for (int c = 0; c < w; ++c) {
+                const int p = s.pp[c], q = s.where[p], a = s.cur[c];
+                s.cur[c] = p;
+                s.cur[q] = a;
+                s.where[p] = c;
+                s.where[a] = q;
+                s.piv[kb + c] = kb + q;
+            }
+            // moved positions: the first w, and the positions swapped with them
+            for (int c = 0; c < w; ++c)
+                if (s.cur[c] != c) {
+                    s.pl[npl] = c;
+                    s.pl[2 * nb + npl] = s.cur[c];
+                    ++npl;
+                }
+            // (where[] is done with: it marks the positions already listed)
+            for (int c = 0; c < w; ++c) {
+                const int q = s.piv[kb + c] - kb;
+                if (q < w || s.cur[q] == q || s.where[q] < 0) continue;
+                s.where[q] = -1;
+                s.pl[npl] = q;
+                s.pl[2 * nb + npl] = s.cur[q];
+                ++npl;
+            }
+            *s_npl = npl;
+        }
+        __syncthreads();
+        // the panel back in its final row order
         for (int t = tid; t < rp * w; t += NT) {
             const int r = t % rp, c = t / rp;
-            A[(kb + r) + (int64_t)(kb + c) * n] = s.P[r + c * ld_p];
+            A[(kb + r) + (int64_t)(kb + c) * n] = s.P[s.cur[r] + c * ld_p];
         }
-        // row interchanges on the columns outside the panel, in pivot order
-        for (int j = tid; j < n - w; j += NT) {
-            const int jj = j < kb ? j : j + w;
-            T* colp = A + (int64_t)jj * n;
-            for (int c = 0; c < w; ++c) {
-                const int pr = s.piv[kb + c];
-                if (pr != kb + c) {
-                    const T t0 = colp[kb + c];
-                    colp[kb + c] = colp[pr];
-                    colp[pr] = t0;
+        __syncthreads();
+        // the moved rows of the columns outside the panel: gather all, then scatter
+        const int npl = *s_npl, nout = n - w;
+        if (npl > 0) {
+            const int per = max(1, cap / npl);  // columns per staging round
+            for (int j0 = 0; j0 < nout; j0 += per) {
+                const int nj = min(per, nout - j0);
+                for (int t = tid; t < npl * nj; t += NT) {
+                    const int e = t % npl, jj = j0 + t / npl;
+                    const int j = jj < kb ? jj : jj + w;
+                    s.P[t] = A[(kb + s.pl[2 * nb + e]) + (int64_t)j * n];
+                }
+                __syncthreads();
+                for (int t = tid; t < npl * nj; t += NT) {
+                    const int e = t % npl, jj = j0 + t / npl;
+                    const int j = jj < kb ? jj : jj + w;
+                    A[(kb + s.pl[e]) + (int64_t)j * n] = s.P[t];
+                }
+                __syncthreads();
+            }
+        }
+        // the factorised panel again, in its final row order
+        for (int t = tid; t < rp * w; t += NT) {
+            const int r = t % rp, c = t / rp;
+            s.P[r + c * ld_p] = A[(kb + r) + (int64_t)(kb + c) * n];
+        }
+        __syncthreads();
+        const int r22 = n - kb - w;
+        if (r22 <= 0) continue;
+        // Li = L11^{-1} (column `lane` by warp 0: forward substitution on e_lane)
+        T* Li = s.D;
+        if (warp == 0) {
+            T y[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) y[i] = i == lane ? (T)1 : (T)0;
+#pragma unroll
+            for (int i = 1; i < 32; ++i) {
+                if (i < w) {
+                    T acc = y[i];
+#pragma unroll
+                    for (int k = 0; k < i; ++k) acc = fma(-s.P[i + k * ld_p], y[k], acc);
+                    y[i] = acc;
                 }
             }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) Li[i + 32 * lane] = y[i];
         }
         __syncthreads();
         // U12 = L11^{-1} A12 and A22 -= L21 U12, one column chunk at a time
-        const int r22 = n - kb - w;
         for (int j0 = kb + w; j0 < n; j0 += CW) {
             const int wc = min(CW, n - j0);
             for (int t = tid; t < w * wc; t += NT) {
@@ -180,13 +275,28 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, double* s_v
                 s.U[r + c * nb] = A[(kb + r) + (int64_t)(j0 + c) * n];
             }
             __syncthreads();
-            if (tid < wc) {
-                T* u = s.U + tid * nb;
-                for (int r = 1; r < w; ++r) {
-                    T acc = u[r];
-                    for (int cc = 0; cc < r; ++cc) acc = fma(-s.P[r + cc * ld_p], u[cc], acc);
-                    u[r] = acc;
+            {
+                // thread: column tid % CW, rows tid / CW + 4 q
+                const int c = tid % CW, r0 = tid / CW;
+                T u[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) u[k] = (c < wc && k < w) ? s.U[k + c * nb] : (T)0;
+                T out[32 / (NT / CW)];
+#pragma unroll
+                for (int q = 0; q < 32 / (NT / CW); ++q) {
+                    const int r = r0 + (NT / CW) * q;
+                    T acc = (T)0;
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) acc = fma(Li[r + 32 * k], u[k], acc);
+                    out[q] = acc;
                 }
+                __syncthreads();
+                if (c < wc)
+#pragma unroll
+                    for (int q = 0; q < 32 / (NT / CW); ++q) {
+                        const int r = r0 + (NT / CW) * q;
+                        if (r < w) s.U[r + c * nb] = out[q];
+                    }
             }
             __syncthreads();
             for (int t = tid; t < w * wc; t += NT) {
@@ -259,20 +369,19 @@ __device__ __forceinline__ void load_diag(const T* A, int n, int c0, int w, T* D
     }
 }
 
-// x <- A^{-1} x using the LU factors in A and s.perm (factors in T, x in
-// FP64; with T = float the products are rounded to the FP32 factors'
-// accuracy).  Blocked substitution: warp 0 solves each 32 x 32 diagonal
-// block (staged in shared memory) with shuffles, then all threads update the
-// rest of x with the block's 32 new entries while the next diagonal block is
-// staged -- two block barriers per 32 columns.
+// x <- A^{-1} x using the LU factors in A and s.perm, in the arithmetic of
+// the factors (T): x is rounded to T on entry and widened back on exit (with
+// T = float this is the correction solve of mixed-precision refinement).
+// Blocked substitution: warp 0 solves each 32 x 32 diagonal block (staged in
+// shared memory) with shuffles, then all threads update the rest of x with
+// the block's 32 new entries while the next diagonal block is staged -- two
+// block barriers per 32 columns.
 template <typename T>
 __device__ void lu_solve(const T* A, int n, Smem<T>& s, double* x) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double* tmp = reinterpret_cast<double*>(s.P);  // the panel is free after the factorisation
-    for (int i = tid; i < n; i += NT) tmp[i] = x[s.perm[i]];
+    T* xs = s.P;  // the panel is free after the factorisation
+    for (int i = tid; i < n; i += NT) xs[i] = (T)x[s.perm[i]];
     load_diag(A, n, 0, min(32, n), s.D);
-    __syncthreads();
-    for (int i = tid; i < n; i += NT) x[i] = tmp[i];
     __syncthreads();
     // L y = P x, L unit lower triangular
     int buf = 0;
@@ -280,19 +389,19 @@ __device__ void lu_solve(const T* A, int n, Smem<T>& s, double* x) {
         const int w = min(32, n - c0);
         const T* D = s.D + buf * 1024;
         if (warp == 0) {
-            double xr = lane < w ? x[c0 + lane] : 0.0;
+            T xr = lane < w ? xs[c0 + lane] : (T)0;
             for (int c = 0; c < w - 1; ++c) {
-                const double xc = __shfl_sync(0xffffffffu, xr, c);
-                if (lane > c) xr = fma(-(double)D[lane + 32 * c], xc, xr);
+                const T xc = __shfl_sync(0xffffffffu, xr, c);
+                if (lane > c) xr = fma(-D[lane + 32 * c], xc, xr);
             }
-            if (lane < w) x[c0 + lane] = xr;
+            if (lane < w) xs[c0 + lane] = xr;
         }
         __syncthreads();
         if (c0 + 32 < n) load_diag(A, n, c0 + 32, min(32, n - c0 - 32), s.D + (buf ^ 1) * 1024);
         for (int r = c0 + w + tid; r < n; r += NT) {
-            double acc = x[r];
-            for (int c = 0; c < w; ++c) acc = fma(-(double)A[r + (int64_t)(c0 + c) * n], x[c0 + c], acc);
-            x[r] = acc;
+            T acc = xs[r];
+            for (int c = 0; c < w; ++c) acc = fma(-A[r + (int64_t)(c0 + c) * n], xs[c0 + c], acc);
+            xs[r] = acc;
         }
         buf ^= 1;
         __syncthreads();
@@ -307,13 +416,13 @@ __device__ void lu_solve(const T* A, int n, Smem<T>& s, double* x) {
         const int c0 = c1 > 32 ? c1 - 32 : 0, w = c1 - c0;
         const T* D = s.D + buf * 1024;
         if (warp == 0) {
-            double xr = lane < w ? x[c0 + lane] : 0.0;
+            T xr = lane < w ? xs[c0 + lane] : (T)0;
             for (int c = w - 1; c >= 0; --c) {
-                if (lane == c) xr = xr / (double)D[c + 32 * c];
-                const double xc = __shfl_sync(0xffffffffu, xr, c);
-                if (lane < c) xr = fma(-(double)D[lane + 32 * c], xc, xr);
+                if (lane == c) xr = xr / D[c + 32 * c];
+                const T xc = __shfl_sync(0xffffffffu, xr, c);
+                if (lane < c) xr = fma(-D[lane + 32 * c], xc, xr);
             }
-            if (lane < w) x[c0 + lane] = xr;
+            if (lane < w) xs[c0 + lane] = xr;
         }
         __syncthreads();
         if (c0 > 0) {
@@ -321,13 +430,15 @@ __device__ void lu_solve(const T* A, int n, Smem<T>& s, double* x) {
             load_diag(A, n, n0, c0 - n0, s.D + (buf ^ 1) * 1024);
         }
         for (int r = tid; r < c0; r += NT) {
-            double acc = x[r];
-            for (int c = 0; c < w; ++c) acc = fma(-(double)A[r + (int64_t)(c0 + c) * n], x[c0 + c], acc);
-            x[r] = acc;
+            T acc = xs[r];
+            for (int c = 0; c < w; ++c) acc = fma(-A[r + (int64_t)(c0 + c) * n], xs[c0 + c], acc);
+            xs[r] = acc;
         }
         buf ^= 1;
         __syncthreads();
     }
+    for (int i = tid; i < n; i += NT) x[i] = (double)xs[i];
+    __syncthreads();
 }
 
 // Entry ((i',j'),(i,j)) of the sample's Ahat^st in FP64 (row i' + a j', column i + a j).
@@ -348,8 +459,9 @@ template <typename T>
 __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
     extern __shared__ double smem[];
     __shared__ double s_val[NWARP];
-    __shared__ int s_idx[NWARP];
-    __shared__ int s_item;
+    __shared__ T s_cv[2][NWARP];
+    __shared__ int s_ci[2][NWARP];
+    __shared__ int s_item, s_npl;
     const int nfull = g.nfull, nb = g.nb;
     Smem<T> s;
     s.P = reinterpret_cast<T*>(smem);
@@ -364,6 +476,10 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
         // 16-byte aligned after the index arrays
         const uintptr_t pd = (reinterpret_cast<uintptr_t>(s.perm + nfull) + 15) & ~(uintptr_t)15;
         s.D = reinterpret_cast<T*>(pd);
+        s.cur = reinterpret_cast<int*>(s.D + 2 * 32 * 32);
+        s.where = s.cur + nfull;
+        s.pl = s.where + nfull;
+        s.pp = s.pl + 4 * nb;
     }
     T* A = reinterpret_cast<T*>(g.ws) + (size_t)blockIdx.x * nfull * nfull;
     const int tid = threadIdx.x;
@@ -405,6 +521,12 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
             s.perm[t] = i | (j << 16);  // (i, j) of index t, until the factorisation
         }
         __syncthreads();
+        // FP32 copy of Ahat(mu) for the FP32 assembly (in the panel buffer,
+        // free until the factorisation): one rounding per entry of Ahat
+        float* ah32 = reinterpret_cast<float*>(s.P);
+        if (g.fp32_asm)
+            for (int t = tid; t < a * a; t += NT) ah32[t] = (float)s.Ah[t];
+        __syncthreads();
         // assemble Ahat^st (FP64, or FP32 products in the FP32-assembly mode)
         for (int64_t t = tid; t < (int64_t)n * n; t += NT) {
             const int row = (int)(t % n), col = (int)(t / n);
@@ -413,7 +535,7 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
                 const int rc = s.perm[row], cc = s.perm[col];
                 const int ip = rc & 0xffff, jp = rc >> 16, i = cc & 0xffff, j = cc >> 16;
                 const int64_t gi = (int64_t)(ip + g.ns * jp) + (int64_t)(i + g.ns * j) * nfull;
-                float f = -(float)s.Ah[ip + i * a] * g.G32[gi];
+                float f = -ah32[ip + i * a] * g.G32[gi];
                 if (ip == i) {
                     const int64_t mi = (int64_t)i * g.nt * g.nt + jp + (int64_t)j * g.nt;
                     f += (float)(g.M[mi] - g.S[mi]);
@@ -426,7 +548,7 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
             A[row + (int64_t)col * n] = v;
         }
         __syncthreads();
-        const bool ok = lu_factor(A, n, nfull, nb, s, s_val, s_idx);
+        const bool ok = lu_factor(A, n, nfull, nb, s, s_cv, s_ci, &s_npl);
         if (!ok) {
             for (int t = tid; t < n; t += NT) up[t] = 0.0;
             if (tid == 0) {
@@ -452,12 +574,16 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
                 const double* Gr = g.G + (ip + (int64_t)g.ns * jp);
                 const double* Ahr = s.Ah + ip;
                 const int64_t mi = (int64_t)ip * g.nt * g.nt + jp;
-                for (int j = 0; j < bt; ++j) {
-                    const double* Gc = Gr + (int64_t)g.ns * j * g.nfull;
-                    const double* xj = s.x + a * j;
-                    for (int i = 0; i < a; ++i) acc = fma(Ahr[i * a] * Gc[(int64_t)i * g.nfull], xj[i], acc);
-                    acc = fma(-(g.M[mi + (int64_t)j * g.nt] - g.S[mi + (int64_t)j * g.nt]), xj[ip], acc);
+                // sum_i Ahat[i', i] (sum_j G[(i',j'),(i,j)] x[i + a j]): one FP64
+                // multiply-add per entry (FP64 issues at 1/64 of the FP32 rate)
+                for (int i = 0; i < a; ++i) {
+                    const double* Gi = Gr + (int64_t)i * g.nfull;
+                    double t = 0.0;
+                    for (int j = 0; j < bt; ++j) t = fma(Gi[(int64_t)g.ns * j * g.nfull], s.x[i + a * j], t);
+                    acc = fma(Ahr[i * a], t, acc);
                 }
+                for (int j = 0; j < bt; ++j)
+                    acc = fma(-(g.M[mi + (int64_t)j * g.nt] - g.S[mi + (int64_t)j * g.nt]), s.x[ip + a * j], acc);
                 s.r[row] = acc;
             }
             __syncthreads();
@@ -520,7 +646,8 @@ size_t solve_smem(int nfull, int ns, int nb, size_t tsize) {
     // the panel also holds one FP64 vector during the triangular solves
     const size_t panel = std::max(tsize * (size_t)nfull * nb, sizeof(double) * (size_t)nfull);
     return panel + tsize * (size_t)nb * CW + sizeof(double) * ((size_t)ns * ns + 3 * (size_t)nfull) +
-           2 * sizeof(int) * (size_t)nfull + 16 + tsize * 2 * 32 * 32 + 64;
+           2 * sizeof(int) * (size_t)nfull + 16 + tsize * 2 * 32 * 32 +
+           sizeof(int) * (2 * (size_t)nfull + 5 * (size_t)nb) + 64;
 }
 
 bool fp32_factors(const st_model* m) { return m->opt.precision == ST_FP32_LU; }
@@ -531,6 +658,8 @@ bool fp32_factors(const st_model* m) { return m->opt.precision == ST_FP32_LU; }
 template <typename T>
 st_status solve_plan(st_model* m, int cap_per_sm, int* nb_out, size_t* smem_out, int* blocks_out) {
     const int ns = m->ns, nfull = ns * m->nt;
+    if (nfull > kRowsPerThread * NT)
+        return st_fail(ST_ERR_ARG, "st_rom_solve: ns*nt = %d above %d", nfull, kRowsPerThread * NT);
     int nb = 32;
     int max_optin = 0;
     ST_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
