@@ -17,6 +17,8 @@ from __future__ import annotations
 
 from typing import Dict, Optional, Tuple
 
+import math
+
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
@@ -75,12 +77,18 @@ def bicgstab(K, b: np.ndarray, x0: np.ndarray, tol: float = 1e-14, maxit: int = 
 
 def fom_march(A: sp.csr_matrix, dt: np.ndarray, B: np.ndarray, F: np.ndarray,
               u0: Optional[np.ndarray] = None, solver: str = "splu", tol: float = 1e-14,
-              maxit: int = 2000, iters: Optional[list] = None) -> np.ndarray:
+              maxit: int = 2000, iters: Optional[list] = None, x0_order: int = 0) -> np.ndarray:
     """Backward-Euler march of Eq. fom.  Returns U (N x Nt) whose column k-1
-    is u^k (Eq. snapshotmat uses the same column order)."""
+    is u^k (Eq. snapshotmat uses the same column order).
+
+    x0_order (BiCGSTAB only) picks the initial iterate of each step: the
+    polynomial of degree o = min(k, x0_order) through the last o + 1 levels,
+    evaluated one step ahead (0: the previous level).  It changes the
+    iteration count, not the solution beyond the stopping tolerance."""
     n = A.shape[0]
     nt_steps = dt.shape[0]
     u = np.zeros(n) if u0 is None else np.asarray(u0, dtype=np.float64).copy()
+    levels = [u.copy()]
     U = np.empty((n, nt_steps), dtype=np.float64)
     eye = sp.identity(n, format="csc")
     cache: Dict[float, object] = {}
@@ -96,7 +104,11 @@ def fom_march(A: sp.csr_matrix, dt: np.ndarray, B: np.ndarray, F: np.ndarray,
             u = np.linalg.solve(K, rhs)
         elif solver == "bicgstab":
             K = (eye - h * A).tocsr()
-            u, it, st = bicgstab(K, rhs, u, tol=tol, maxit=maxit)
+            o = min(k, x0_order)
+            x0 = np.zeros(n)
+            for i in range(o + 1):
+                x0 += (-1) ** i * math.comb(o + 1, i + 1) * levels[-1 - i]
+            u, it, st = bicgstab(K, rhs, x0, tol=tol, maxit=maxit)
             if st != "ok":
                 raise RuntimeError(f"oracle BiCGSTAB {st} at step {k + 1}")
             if iters is not None:
@@ -104,6 +116,7 @@ def fom_march(A: sp.csr_matrix, dt: np.ndarray, B: np.ndarray, F: np.ndarray,
         else:
             raise ValueError(solver)
         U[:, k] = u
+        levels = (levels + [u.copy()])[-(x0_order + 1):]
     return U
 
 

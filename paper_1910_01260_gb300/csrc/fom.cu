@@ -27,6 +27,16 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NSLOT = 2;
+// Initial iterate of step k: the polynomial of degree kPred through the last
+// kPred + 1 levels, evaluated one step ahead,
+//   x0 = sum_{i=0}^{o} (-1)^i C(o+1, i+1) u^{k-i},  o = min(k, kPred),
+// which only shortens the Krylov iteration (the stopping test is on the true
+// system).
+#ifndef ST_FOM_PRED_ORDER
+#define ST_FOM_PRED_ORDER 4
+#endif
+constexpr int kPred = ST_FOM_PRED_ORDER;
+constexpr int kHist = kPred + 1;  // levels kept
 #ifndef ST_FOM_BLOCKS_PER_SM
 #define ST_FOM_BLOCKS_PER_SM 2
 #endif
@@ -52,7 +62,7 @@ struct FomArgs {
     const double* B;  // [N x n_in]
     const double* F;  // [Nt x n_in]
     double *x, *r, *rh, *p, *v, *s, *t;  // [N * LD]
-    double* hist;                        // [3 x N * LD] solutions of the last three levels
+    double* hist;                        // [kHist x N * LD] solutions of the last kHist levels
     double* partial;                     // [2 x grid * NSLOT * LD]
     double* snap;
     int n_mu;
@@ -239,24 +249,30 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
     ROWS_END
     for (int k = 0; k < a.Nt; ++k) {
         const double h = a.dt[k];
-        const double* uk = a.hist + (size_t)(k % 3) * vecsz;  // the previous level u^k
-        // ---- Phase X0: initial iterate by extrapolating the last levels in
-        // time (quadratic from the third step on), which only shortens the
-        // Krylov iteration; the stopping test is on the true system
+        const double* uk = a.hist + (size_t)(k % kHist) * vecsz;  // the previous level u^k
+        // ---- Phase X0: initial iterate by extrapolating the last levels in time
         if (k > 0) {
-            const double* ukm1 = a.hist + (size_t)((k + 2) % 3) * vecsz;
-            const double* ukm2 = a.hist + (size_t)((k + 1) % 3) * vecsz;
+            const int o = min(k, kPred);
+            double coef[kPred + 1];  // (-1)^i C(o+1, i+1)
+            {
+                double bin = 1.0;  // C(o+1, i) as i grows
+#pragma unroll
+                for (int i = 0; i <= kPred; ++i) {
+                    bin = bin * (double)(o + 1 - i) / (double)(i + 1);  // C(o+1, i+1)
+                    coef[i] = i <= o ? ((i & 1) ? -bin : bin) : 0.0;
+                }
+            }
             ROWS_BEGIN
-                double x0[VEC], u1[VEC], u2[VEC];
-                ld_vec<VEC>(uk + vi, x0);
-                ld_vec<VEC>(ukm1 + vi, u1);
-                if (k > 1) {
-                    ld_vec<VEC>(ukm2 + vi, u2);
+                double x0[VEC];
 #pragma unroll
-                    for (int u = 0; u < VEC; ++u) x0[u] = fma(3.0, x0[u] - u1[u], u2[u]);
-                } else {
+                for (int u = 0; u < VEC; ++u) x0[u] = 0.0;
 #pragma unroll
-                    for (int u = 0; u < VEC; ++u) x0[u] = fma(2.0, x0[u], -u1[u]);
+                for (int i = 0; i <= kPred; ++i) {
+                    if (i > o) break;
+                    double ui[VEC];
+                    ld_vec<VEC>(a.hist + (size_t)((k - i + kHist * kPred) % kHist) * vecsz + vi, ui);
+#pragma unroll
+                    for (int u = 0; u < VEC; ++u) x0[u] = fma(coef[i], ui[u], x0[u]);
                 }
                 st_vec<VEC>(a.x + vi, x0);
             ROWS_END
@@ -545,7 +561,7 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
                 if (p < a.n_mu) __stcs(a.snap + ((int64_t)p * a.Nt + k) * N + row, xv[u]);
             }
             if (changed) st_vec<VEC>(a.x + vi, xv);
-            st_vec<VEC>(a.hist + (size_t)((k + 1) % 3) * vecsz + vi, xv);
+            st_vec<VEC>(a.hist + (size_t)((k + 1) % kHist) * vecsz + vi, xv);
         ROWS_END
         if (blockIdx.x == 0 && threadIdx.x < a.n_mu) {
             const int p = threadIdx.x;
@@ -601,12 +617,12 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     const int64_t rpb = Cfg<LD>::RPB;
     const int64_t nchunks = (N + rpb - 1) / rpb;
     if (blocks > nchunks) blocks = (int)std::max<int64_t>(1, nchunks);
-    size_t need = sizeof(double) * ((size_t)mx * LD + 10 * vec + 2 * (size_t)blocks * NSLOT * LD) + 1024;
+    size_t need = sizeof(double) * ((size_t)mx * LD + (7 + kHist) * vec + 2 * (size_t)blocks * NSLOT * LD) + 1024;
     ST_TRY(st_grow(m, m->ws_fom, need));
     double* base = (double*)m->ws_fom.p;
     double* amu = base;
     double* vecs = amu + (size_t)mx * LD;
-    double* partial = vecs + 10 * vec;
+    double* partial = vecs + (7 + kHist) * vec;
     int sblocks = (int)std::min<int64_t>((std::max(mx, N) * LD + 255) / 256, 8 * m->num_sms);
     {
         ST_PROF(m, "fom_setup_kernel");

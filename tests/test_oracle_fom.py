@@ -86,3 +86,34 @@ def test_nonuniform_steps():
     U = fom.fom_march(A, dt, p.B, p.F, p.u0)
     ref = p.u0 / np.prod(1.0 + dt)
     assert np.abs(U[:, -1] - ref).max() < 1e-15
+
+
+def test_bicgstab_polynomial_initial_iterate():
+    # With A = 0 the march is u^k = u^{k-1} + dt B f^k; choosing f so that u^k
+    # is a cubic in k, the extrapolation of degree >= 3 through the previous
+    # levels is exact, so BiCGSTAB starts converged (0 iterations) from the
+    # fifth step on, while from the previous level it needs one iteration.
+    n, nt = 6, 10
+    rng = np.random.default_rng(2)
+    c = rng.standard_normal((4, n))
+    ks = np.arange(nt + 1, dtype=float)
+    traj = np.stack([c[0] + c[1] * k + c[2] * k ** 2 + c[3] * k ** 3 for k in ks])  # u^0..u^nt
+    dt = np.ones(nt)
+    B = np.eye(n)
+    F = traj[1:] - traj[:-1]
+    A = fom.sp.csr_matrix((n, n))
+    for order, want in ((4, 0), (0, 1)):
+        its = []
+        U = fom.fom_march(A, dt, B, F, traj[0], solver="bicgstab", tol=1e-12, iters=its, x0_order=order)
+        assert np.abs(U.T - traj[1:]).max() < 1e-9 * np.abs(traj).max()
+        assert all(i == want for i in its[4:]), its
+    # and on a transport problem the solution does not depend on it
+    p = problem_for("c1")
+    A = _A(p, p.test_mu[0])
+    U1 = fom.fom_march(A, p.dt[:12], p.B, p.F[:12], p.u0, solver="splu")
+    its0, its4 = [], []
+    U0 = fom.fom_march(A, p.dt[:12], p.B, p.F[:12], p.u0, solver="bicgstab", tol=1e-14, iters=its0)
+    U4 = fom.fom_march(A, p.dt[:12], p.B, p.F[:12], p.u0, solver="bicgstab", tol=1e-14, iters=its4, x0_order=4)
+    s = np.abs(U1).max()
+    assert np.abs(U0 - U1).max() / s < 1e-12 and np.abs(U4 - U1).max() / s < 1e-12
+    assert sum(its4) < sum(its0)
