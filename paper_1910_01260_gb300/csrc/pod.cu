@@ -141,6 +141,39 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
             __stcg(part(a.m + 1), t2);
         }
     };
+    // fixed-order sum over the blocks of one partial slot (lane-strided, then
+    // across the warp); the loads of four blocks are in flight together
+    auto sum_slot = [&](int slot) -> double {
+        double acc = 0.0;
+        for (int b0 = lane; b0 < G; b0 += 4 * 32) {
+            double v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int bb = b0 + 32 * i;
+                v[i] = bb < G ? __ldcg(part_of(bb, slot)) : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc += v[i];
+        }
+        return warp_sum(acc);
+    };
+    // dot product of this block's rows of two columns (lane-strided, then
+    // across the warp), four rows' loads in flight together
+    auto block_dot = [&](const double* x, const double* y) -> double {
+        double acc = 0.0;
+        for (int64_t i0 = r0 + lane; i0 < r1; i0 += 4 * 32) {
+            double xv[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + 32 * u;
+                xv[u] = i < r1 ? __ldcg(x + i) : 0.0;
+                yv[u] = i < r1 ? __ldcg(y + i) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc = fma(xv[u], yv[u], acc);
+        }
+        return warp_sum(acc);
+    };
     int k = 0;   // directions found so far
     int kc = 0;  // directions the finishing column was projected on
     {
@@ -159,23 +192,13 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         // reduction A: ||e_j||^2, e_j^T e_{j+1}, J(:, 0:k)^T e_{j+1}
         if (!grid_sync(a.bar, &s_flag)) return;
         const int kn = k;
-        for (int c = warp; c < kn; c += NWARP) {
-            double acc = 0.0;
-            for (int bb = lane; bb < G; bb += 32) acc += __ldcg(part_of(bb, c));
-            acc = warp_sum(acc);
-            if (lane == 0) hn[c] = acc;
-        }
-        if (warp == 0) {
-            double s1 = 0.0, s2 = 0.0;
-            for (int bb = lane; bb < G; bb += 32) {
-                s1 += __ldcg(part_of(bb, a.m));
-                s2 += __ldcg(part_of(bb, a.m + 1));
-            }
-            s1 = warp_sum(s1);
-            s2 = warp_sum(s2);
+        // slots 0..kn-1: coefficients; then the squared norm and the cross term
+        for (int c = warp; c < kn + 2; c += NWARP) {
+            const double acc = sum_slot(c < kn ? c : a.m + (c - kn));
             if (lane == 0) {
-                s_nu = sqrt(s1);
-                s_cross = s2;
+                if (c < kn) hn[c] = acc;
+                else if (c == kn) s_nu = sqrt(acc);
+                else s_cross = acc;
             }
         }
         ++red;
@@ -210,18 +233,13 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
             }
             __syncthreads();
             for (int c = warp; c < k; c += NWARP) {
-                const double* jc = a.J + (int64_t)c * a.N;
-                double acc = 0.0;
-                for (int64_t i = r0 + lane; i < r1; i += 32) acc = fma(__ldcg(jc + i), __ldcg(e + i), acc);
-                acc = warp_sum(acc);
+                const double acc = block_dot(a.J + (int64_t)c * a.N, e);
                 if (lane == 0) __stcg(part(c), acc);
             }
             // reduction B: J(:, 0:k)^T e_{j+1} (second pass)
             if (!grid_sync(a.bar, &s_flag)) return;
             for (int c = warp; c < k; c += NWARP) {
-                double acc = 0.0;
-                for (int bb = lane; bb < G; bb += 32) acc += __ldcg(part_of(bb, c));
-                acc = warp_sum(acc);
+                const double acc = sum_slot(c);
                 if (lane == 0) h2n[c] = acc;
             }
             ++red;
@@ -243,10 +261,7 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         }
         if (e2)
             for (int c = warp; c < k; c += NWARP) {
-                const double* jc = a.J + (int64_t)c * a.N;
-                double acc = 0.0;
-                for (int64_t i = r0 + lane; i < r1; i += 32) acc = fma(__ldcg(jc + i), __ldcg(e2 + i), acc);
-                acc = warp_sum(acc);
+                const double acc = block_dot(a.J + (int64_t)c * a.N, e2);
                 if (lane == 0) __stcg(part(c), acc);
             }
         write_pair(n2, cr);
