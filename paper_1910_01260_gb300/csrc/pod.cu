@@ -347,15 +347,6 @@ __global__ void build_qt_kernel(int r, int k, int m, const double* __restrict__ 
     }
 }
 
-__global__ void eye_kernel(int n, double* Y, int ldy) {
-    const int64_t tot = (int64_t)n * n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t % n), j = (int)(t / n);
-        Y[i + (int64_t)j * ldy] = i == j ? 1.0 : 0.0;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Householder QR with column pivoting of X (m x n, m >= n), in place and
 // without moving columns: logical column k of X Pi is physical column
@@ -522,31 +513,42 @@ __global__ void build_rt_kernel(int n, const double* __restrict__ X, int ldx, co
     }
 }
 
-// B (m x nc) <- Q1 B = H_0 H_1 ... H_{n-1} B: the reflectors of qrp_kernel
-// in reverse order, one warp per column of B, each reflector staged once per
-// CTA in shared memory.
-__global__ void __launch_bounds__(128) apply_q_kernel(int m, int n, int nc, const double* __restrict__ X,
-                                                      int ldx, const int* __restrict__ piv,
-                                                      const double* __restrict__ tau,
-                                                      const double* __restrict__ scale, double* B, int ldb) {
-    extern __shared__ double v[];  // [m]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int c = blockIdx.x * nw + warp;
-    double* bc = B + (int64_t)c * ldb;
-    for (int k = n - 1; k >= 0; --k) {
-        const double t = tau[k];
-        if (t == 0.0) continue;
-        const double* x = X + (int64_t)piv[k] * ldx;
-        const double sc = scale[k];
+// The reflectors of qrp_kernel as the columns of Y (m x n, ld ldy): column k
+// is v_k = e_k + (x_k scaled) below row k, zero above; zero for a skipped
+// reflector (tau_k = 0), so H_k = I - tau_k v_k v_k^T.
+__global__ void build_wy_kernel(int m, int n, const double* __restrict__ X, int ldx, const int* __restrict__ piv,
+                                const double* __restrict__ tau, const double* __restrict__ scale, double* Y,
+                                int ldy) {
+    const int64_t tot = (int64_t)m * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t % m), k = (int)(t / m);
+        double v = 0.0;
+        if (tau[k] != 0.0 && i >= k) v = i == k ? 1.0 : X[i + (int64_t)piv[k] * ldx] * scale[k];
+        Y[i + (int64_t)k * ldy] = v;
+    }
+}
+
+// Triangular factor of a block of b reflectors (LAPACK's forward, columnwise
+// larft): H_0 H_1 ... H_{b-1} = I - Y T Y^T with T upper triangular,
+// T(j, j) = tau_j, T(0:j, j) = -tau_j T(0:j, 0:j) (Y(:, 0:j)^T v_j), from the
+// Gram matrix G = Y^T Y (b x b, ld ldg).  One CTA, b <= 64.
+__global__ void __launch_bounds__(64) larft_kernel(int b, const double* __restrict__ G, int ldg,
+                                                   const double* __restrict__ tau, double* T, int ldt) {
+    __shared__ double z[64];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < b * b; t += blockDim.x) T[t % b + (int64_t)(t / b) * ldt] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        const double tj = tau[j];
+        if (tid < j) z[tid] = -tj * G[tid + (int64_t)j * ldg];
         __syncthreads();
-        for (int i = k + threadIdx.x; i < m; i += blockDim.x) v[i] = i == k ? 1.0 : x[i] * sc;
-        __syncthreads();
-        if (c < nc) {
-            double w = 0.0;
-            for (int i = k + lane; i < m; i += 32) w = fma(v[i], bc[i], w);
-            w = warp_sum(w) * t;
-            for (int i = k + lane; i < m; i += 32) bc[i] = fma(-w, v[i], bc[i]);
+        if (tid < j) {
+            double acc = 0.0;
+            for (int i = tid; i < j; ++i) acc = fma(T[tid + (int64_t)i * ldt], z[i], acc);
+            T[tid + (int64_t)j * ldt] = acc;
         }
+        if (tid == 0) T[j + (int64_t)j * ldt] = tj;
+        __syncthreads();
     }
 }
 
@@ -1273,18 +1275,38 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
             ncols, mrows, rnew, d_perm, d_piv, d_sig_sorted, Y, cap, Z, cap, Ysel, cap, Vsel, cap);
         ST_TRY(st_check_launch("gather"));
         {
-            // Vsel <- Q1 Vsel, the reflectors of the QR applied in reverse order
-            ST_PROF(m, "apply_q_kernel");
-            const int wpb = 4;
-            const size_t smem = sizeof(double) * mrows;
-            if (smem > 48 * 1024)
-                ST_CUDA_TRY(cudaFuncSetAttribute(apply_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            apply_q_kernel<<<(rnew + wpb - 1) / wpb, 32 * wpb, smem, st>>>(mrows, ncols, rnew, X, cap, d_piv, q_tau,
-                                                                          q_scale, Vsel, cap);
-            ST_TRY(st_check_launch("apply_q"));
-            double fl = 0.0;
-            for (int kk = 0; kk < ncols; ++kk) fl += 4.0 * (mrows - kk);
-            st_prof_flops(m, "apply_q_kernel", fl * rnew);
+            // Vsel <- Q1 Vsel = H_0 ... H_{n-1} Vsel in blocks of kWy
+            // reflectors in the compact WY form Q_b = I - Y_b T_b Y_b^T, last
+            // block first: Vsel -= Y_b (T_b (Y_b^T Vsel)), the products on the
+            // FP64 GEMM path.  Z (free after the gather) holds the
+            // reflectors; the block temporaries live in ws_pod2 (used
+            // otherwise only by the assembly).
+            constexpr int kWy = 64;
+            double* Yall = Z;  // [mrows x ncols], ld cap
+            ST_TRY(st_grow(m, m->ws_pod2, sizeof(double) * (2 * (size_t)kWy * rnew + 2 * (size_t)kWy * kWy)));
+            double* Wt = (double*)m->ws_pod2.p;           // [kWy x rnew]
+            double* Wt2 = Wt + (size_t)kWy * rnew;        // [kWy x rnew]
+            double* Gb = Wt2 + (size_t)kWy * rnew;        // [kWy x kWy]
+            double* Tb = Gb + (size_t)kWy * kWy;          // [kWy x kWy]
+            {
+                ST_PROF(m, "apply_q_wy_kernels");
+                build_wy_kernel<<<grid_for(m, (int64_t)mrows * ncols), 256, 0, st>>>(mrows, ncols, X, cap, d_piv,
+                                                                                   q_tau, q_scale, Yall, cap);
+                ST_TRY(st_check_launch("build_wy"));
+            }
+            for (int k0 = ((ncols - 1) / kWy) * kWy; k0 >= 0; k0 -= kWy) {
+                const int b = std::min(kWy, ncols - k0), rows_b = mrows - k0;
+                const double* Yb = Yall + k0 + (size_t)k0 * cap;  // rows k0.. (zero above)
+                ST_TRY(st_dgemm(m, true, false, b, b, rows_b, 1.0, Yb, cap, Yb, cap, 0.0, Gb, kWy));
+                {
+                    ST_PROF(m, "apply_q_wy_kernels");
+                    larft_kernel<<<1, 64, 0, st>>>(b, Gb, kWy, q_tau + k0, Tb, kWy);
+                    ST_TRY(st_check_launch("larft"));
+                }
+                ST_TRY(st_dgemm(m, true, false, b, rnew, rows_b, 1.0, Yb, cap, Vsel + k0, cap, 0.0, Wt, kWy));
+                ST_TRY(st_dgemm(m, false, false, b, rnew, b, 1.0, Tb, kWy, Wt, kWy, 0.0, Wt2, kWy));
+                ST_TRY(st_dgemm(m, false, false, rows_b, rnew, b, -1.0, Yb, cap, Wt2, kWy, 1.0, Vsel + k0, cap));
+            }
         }
         // W2 = [W J] Ysel
         ST_TRY(st_dgemm(m, false, false, N, rnew, ncols, 1.0, W, N, Ysel, cap, 0.0, W2, N));
