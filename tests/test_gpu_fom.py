@@ -163,3 +163,27 @@ def test_fom_term_split_random_affine_operator():
         ref = fom.fom_march(A, dt, Bm, F, None)
         assert rel_max(got[k], ref) < TOL
     m.close()
+
+
+def test_fom_barrier_wait_runs_out_and_model_recovers():
+    # A grid barrier allowed a single poll gives up (no CTA can arrive in
+    # time): the march stops with ST_ERR_TIMEOUT instead of hanging, and the
+    # same model marches normally once the limit is restored.  The march has
+    # no asynchronous copies in flight, so CTAs that stop early leave nothing
+    # behind.
+    import paper_1910_01260_gb300 as st
+    p = make_problem(dim=2, M=8, quad="s4", Nt=4, source="gaussian", g="ramp")
+    mus = p.train_mu[:3]
+    m = make_model(p, spin_limit=1)
+    with pytest.raises(st.StError) as e:
+        gpu_fom(m, p, mus)
+        m.st_sync()
+    assert e.value.code == st.ST_ERR_TIMEOUT
+    m.st_sync()  # the error word was read and cleared
+    m.st_model_set_options(spin_limit=20000000)
+    got, status, _ = gpu_fom(m, p, mus)
+    assert (status == 0).all()
+    ref = oracle_fom(p, mus, Nt=4)
+    for g, r in zip(got, ref):
+        assert rel_max(g, r) < TOL
+    m.close()
