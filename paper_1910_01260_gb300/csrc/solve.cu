@@ -23,7 +23,8 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
-constexpr int CW = 64;  // trailing-update column chunk
+constexpr int CW = 64;       // trailing-update column chunk
+constexpr int CWP = CW + 1;  // row stride of the chunk's U12 in shared memory
 
 struct SolveArgs {
     int n_mu, Q, ns, nt, nfull;
@@ -50,7 +51,7 @@ struct SolveArgs {
 template <typename T>
 struct Smem {
     T* P;         // panel: nfull x nb (ld nfull)
-    T* U;         // nb x CW
+    T* U;         // nb x CW, row stride CWP
     double* Ah;   // ns_p x ns_p
     double* b;    // rhs
     double* x;    // solution
@@ -267,12 +268,14 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[N
             for (int i = 0; i < 32; ++i) Li[i + 32 * lane] = y[i];
         }
         __syncthreads();
-        // U12 = L11^{-1} A12 and A22 -= L21 U12, one column chunk at a time
+        // U12 = L11^{-1} A12 and A22 -= L21 U12, one column chunk at a time.
+        // U12 of the chunk is kept row by row (row stride CWP = CW + 1, so
+        // both the column-wise and the row-wise accesses are conflict free).
         for (int j0 = kb + w; j0 < n; j0 += CW) {
             const int wc = min(CW, n - j0);
             for (int t = tid; t < w * wc; t += NT) {
                 const int r = t % w, c = t / w;
-                s.U[r + c * nb] = A[(kb + r) + (int64_t)(j0 + c) * n];
+                s.U[r * CWP + c] = A[(kb + r) + (int64_t)(j0 + c) * n];
             }
             __syncthreads();
             {
@@ -280,7 +283,7 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[N
                 const int c = tid % CW, r0 = tid / CW;
                 T u[32];
 #pragma unroll
-                for (int k = 0; k < 32; ++k) u[k] = (c < wc && k < w) ? s.U[k + c * nb] : (T)0;
+                for (int k = 0; k < 32; ++k) u[k] = (c < wc && k < w) ? s.U[k * CWP + c] : (T)0;
                 T out[32 / (NT / CW)];
 #pragma unroll
                 for (int q = 0; q < 32 / (NT / CW); ++q) {
@@ -295,49 +298,50 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[N
 #pragma unroll
                     for (int q = 0; q < 32 / (NT / CW); ++q) {
                         const int r = r0 + (NT / CW) * q;
-                        if (r < w) s.U[r + c * nb] = out[q];
+                        if (r < w) s.U[r * CWP + c] = out[q];
                     }
             }
             __syncthreads();
             for (int t = tid; t < w * wc; t += NT) {
                 const int r = t % w, c = t / w;
-                A[(kb + r) + (int64_t)(j0 + c) * n] = s.U[r + c * nb];
+                A[(kb + r) + (int64_t)(j0 + c) * n] = s.U[r * CWP + c];
             }
-            const int tx = tid & 15, ty = tid >> 4;
-            for (int rt = 0; rt < r22; rt += 64) {
-                T acc[4][4];
+            // A22 -= L21 U12: thread (rg, cg) owns rows RT rg .. RT rg + RT - 1
+            // and columns 8 cg .. 8 cg + 7 of a (32 RT) x 64 tile; the tile's
+            // old values are loaded first (one round of independent loads)
+            // and updated in registers
+            constexpr int RT = sizeof(T) == 4 ? 8 : 4;  // FP64: fewer rows (registers)
+            const int cg = tid % 8, rg = tid / 8;
+            for (int rt = 0; rt < r22; rt += 32 * RT) {
+                const int rb = rt + RT * rg;  // first row (of A22) of this thread
+                if (rb < r22 && 8 * cg < wc) {
+                    T acc[RT][8];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                    for (int a2 = 0; a2 < RT; ++a2)
 #pragma unroll
-                    for (int bq = 0; bq < 4; ++bq) acc[a][bq] = (T)0;
-                for (int cc = 0; cc < w; ++cc) {
-                    T lv[4], uv[4];
+                        for (int b2 = 0; b2 < 8; ++b2) {
+                            const int rr = rb + a2, c2 = 8 * cg + b2;
+                            acc[a2][b2] = (rr < r22 && c2 < wc) ? A[(kb + w + rr) + (int64_t)(j0 + c2) * n] : (T)0;
+                        }
+                    for (int cc = 0; cc < w; ++cc) {
+                        T lv[RT], uv[8];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int rr = rt + tx + 16 * a;
-                        lv[a] = rr < r22 ? s.P[(w + rr) + cc * ld_p] : (T)0;
+                        for (int a2 = 0; a2 < RT; ++a2)
+                            lv[a2] = rb + a2 < r22 ? s.P[(w + rb + a2) + cc * ld_p] : (T)0;
+#pragma unroll
+                        for (int b2 = 0; b2 < 8; ++b2) uv[b2] = s.U[cc * CWP + 8 * cg + b2];
+#pragma unroll
+                        for (int a2 = 0; a2 < RT; ++a2)
+#pragma unroll
+                            for (int b2 = 0; b2 < 8; ++b2) acc[a2][b2] = fma(-lv[a2], uv[b2], acc[a2][b2]);
                     }
 #pragma unroll
-                    for (int bq = 0; bq < 4; ++bq) {
-                        const int c2 = ty + 16 * bq;
-                        uv[bq] = c2 < wc ? s.U[cc + c2 * nb] : (T)0;
-                    }
+                    for (int a2 = 0; a2 < RT; ++a2)
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
-#pragma unroll
-                        for (int bq = 0; bq < 4; ++bq) acc[a][bq] = fma(lv[a], uv[bq], acc[a][bq]);
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int rr = rt + tx + 16 * a;
-                    if (rr >= r22) continue;
-#pragma unroll
-                    for (int bq = 0; bq < 4; ++bq) {
-                        const int c2 = ty + 16 * bq;
-                        if (c2 >= wc) continue;
-                        T* p = A + (kb + w + rr) + (int64_t)(j0 + c2) * n;
-                        *p -= acc[a][bq];
-                    }
+                        for (int b2 = 0; b2 < 8; ++b2) {
+                            const int rr = rb + a2, c2 = 8 * cg + b2;
+                            if (rr < r22 && c2 < wc) A[(kb + w + rr) + (int64_t)(j0 + c2) * n] = acc[a2][b2];
+                        }
                 }
             }
             __syncthreads();
@@ -466,7 +470,7 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
     Smem<T> s;
     s.P = reinterpret_cast<T*>(smem);
     s.U = s.P + (size_t)nfull * nb;
-    s.Ah = reinterpret_cast<double*>(s.U + (size_t)nb * CW);
+    s.Ah = reinterpret_cast<double*>(s.U + (size_t)nb * CWP);  // nb * CWP * sizeof(T) is a multiple of 8
     s.b = s.Ah + (size_t)g.ns * g.ns;
     s.x = s.b + nfull;
     s.r = s.x + nfull;
@@ -645,7 +649,7 @@ __global__ void size_scatter_kernel(int n_mu, const int* __restrict__ npv, int* 
 size_t solve_smem(int nfull, int ns, int nb, size_t tsize) {
     // the panel also holds one FP64 vector during the triangular solves
     const size_t panel = std::max(tsize * (size_t)nfull * nb, sizeof(double) * (size_t)nfull);
-    return panel + tsize * (size_t)nb * CW + sizeof(double) * ((size_t)ns * ns + 3 * (size_t)nfull) +
+    return panel + tsize * (size_t)nb * CWP + sizeof(double) * ((size_t)ns * ns + 3 * (size_t)nfull) +
            2 * sizeof(int) * (size_t)nfull + 16 + tsize * 2 * 32 * 32 +
            sizeof(int) * (2 * (size_t)nfull + 5 * (size_t)nb) + 64;
 }
