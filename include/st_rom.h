@@ -130,8 +130,11 @@ st_status st_sync(st_model* m);
 /* Full-order snapshot march (Eq. fom):
  *   (I - dt_k A(mu_p)) u^k = u^{k-1} + dt_k B f^k,  k = 1..Nt, t_k = sum dt_j,
  * for n_mu parameter samples marched together; each step is solved by
- * BiCGSTAB (initial guess u^{k-1}) on the sliced-ELL operator, with all
- * iteration control on the device.
+ * BiCGSTAB on the sliced-ELL operator, with all iteration control on the
+ * device, from the initial iterate x0 = sum_{i=0}^{o} (-1)^i C(o+1, i+1)
+ * u^{k-1-i}, o = min(k-1, 4) (the degree-o extrapolation of the previous
+ * levels, u^0 = u0; x0 = u0 at the first step); the stopping test
+ * ||r|| <= tol ||rhs|| is on the true system.
  *   theta     host [n_mu x Q] row major: theta_q(mu_p) at theta[p*Q + q]
  *   dt        host [Nt] time steps
  *   u0        dev  [N] initial state shared by all samples, or NULL for 0
