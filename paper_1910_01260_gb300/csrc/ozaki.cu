@@ -37,7 +37,7 @@ namespace {
 constexpr int kSlices = 8;  // digits per entry
 constexpr int kDiags = 8;   // kept diagonals D = 0..7
 constexpr int kBM = 128, kBN = 64, kBK = 64;
-constexpr int kChunk = 448;  // K of one exact accumulation (7 stages)
+constexpr int kChunk = 448;  // longest K of one exact accumulation (7 stages)
 constexpr int kARing = 6;    // A digit-plane tiles in flight
 constexpr int kThreads = 256;  // 8 warps: two per 32-lane quarter of the accumulators
 constexpr uint32_t kTileA = kBM * kBK * 2;      // one digit plane of the A tile (16 KB)
@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(256) split_kernel(int64_t R, int64_t K, int64_
 
 struct OzArgs {
     int M, N, K;
+    int chunk;          // K per CTA: a multiple of kBK, at most kChunk
     const int32_t* ea;  // [M] exponent fields of the rows of op(A)
     const int32_t* eb;  // [N] exponent fields of the columns of op(B)
     double alpha, beta;
@@ -247,8 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const __grid_const
     const uint32_t b_full = tc::smem_u32(&bars[2 * kARing]), b_empty = tc::smem_u32(&bars[2 * kARing + 2]);
     const uint32_t done = tc::smem_u32(&bars[2 * kARing + 4]);
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, chunk = blockIdx.z;
-    const int kbeg = chunk * kChunk;
-    const int klen = min(kChunk, g.K - kbeg);
+    const int kbeg = chunk * g.chunk;
+    const int klen = min(g.chunk, g.K - kbeg);
     const int nks = (klen + kBK - 1) / kBK;
     const int nA = nks * kSlices;
 
@@ -426,7 +427,25 @@ st_status st_ozaki_gemm(st_model* m, bool transA, bool transB, int64_t M, int64_
     // K padded to whole stages with zero digits; the rows of the planes are
     // not padded: the TMA boxes past the last row read zeros
     const int64_t Kp = (K + kBK - 1) / kBK * kBK;
-    const int64_t chunks = (K + kChunk - 1) / kChunk;
+    // K per CTA: the whole stages (up to kChunk) that minimise the waves of
+    // CTAs over the SMs times the work of one CTA (its stages plus ~2 stages
+    // of epilogue); a long-K product with few output tiles gets shorter
+    // chunks so that its CTAs fill the SMs
+    int64_t chunk = kChunk;
+    {
+        const int64_t tiles = ((M + kBM - 1) / kBM) * ((Nc + kBN - 1) / kBN);
+        double best = 1e300;
+        for (int s = kChunk / kBK; s >= 1; --s) {
+            const int64_t c = (int64_t)s * kBK, nch = (K + c - 1) / c;
+            const int64_t waves = (tiles * nch + m->num_sms - 1) / m->num_sms;
+            const double cost = (double)waves * (std::min<int64_t>(s, (K + kBK - 1) / kBK) + 2);
+            if (cost < best - 1e-9) {
+                best = cost;
+                chunk = c;
+            }
+        }
+    }
+    const int64_t chunks = (K + chunk - 1) / chunk;
     if (Kp / kTile > 65535 || (Nc + kBN - 1) / kBN > 65535 || chunks > 65535)
         return st_fail(ST_ERR_ARG, "st_ozaki_gemm: grid too large");
     if (slotA >= kOzSlots) return st_fail(ST_ERR_ARG, "st_ozaki_gemm: bad operand slot");
@@ -494,7 +513,7 @@ st_status st_ozaki_gemm(st_model* m, bool transA, bool transB, int64_t M, int64_
     CUtensorMap ta, tb;
     ST_TRY(st_tmap_bf16_3d(&ta, planesA, Kp, M, kSlices, Kp, M * Kp, kBK, kBM, 1));
     ST_TRY(st_tmap_bf16_3d(&tb, planesB, Kp, Nc, kSlices, Kp, Nc * Kp, kBK, kBN, kSlices));
-    OzArgs g{(int)M, (int)Nc, (int)K, ea, eb, alpha, beta, C, ldc, part, m->d_err, m->opt.spin_limit};
+    OzArgs g{(int)M, (int)Nc, (int)K, (int)chunk, ea, eb, alpha, beta, C, ldc, part, m->d_err, m->opt.spin_limit};
     {
         ST_PROF(m, "ozaki_gemm_kernel");
         st_prof_flops(m, "ozaki_gemm_kernel", 2.0 * (double)M * (double)Nc * (double)K);
