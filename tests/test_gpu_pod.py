@@ -18,9 +18,9 @@ def _snap_tensor(blocks):
     return dev_tensor(np.stack([b.T for b in blocks]))   # (n_mu, Nt, N) = column p*Nt + k
 
 
-def _compare(p, blocks, r_max, ns, nt, sig_tol=1e-11, vec_tol=1e-9, proj_tol=1e-8):
+def _compare(p, blocks, r_max, ns, nt, sig_tol=1e-11, vec_tol=1e-9, proj_tol=1e-8, **opts):
     torch = __import__("torch")
-    m = make_model(p, r_max=r_max)
+    m = make_model(p, r_max=r_max, **opts)
     sig, r = m.st_rom_build_basis(len(blocks), blocks[0].shape[1], _snap_tensor(blocks), ns, nt)
     ref = pod.pod_block_incremental(blocks, ns, nt, r_max=r_max)
     s0 = ref["sigma"][0]
@@ -47,10 +47,11 @@ def _compare(p, blocks, r_max, ns, nt, sig_tol=1e-11, vec_tol=1e-9, proj_tol=1e-
     return sig, r, Wm, Vm, ref
 
 
-def test_pod_c1_untruncated():
+@pytest.mark.parametrize("fp64_gemm", [1, 0])  # tensor-core products, FP64 SIMT products
+def test_pod_c1_untruncated(fp64_gemm):
     p = problem_for("c1")
     blocks = oracle_fom(p, p.train_mu)
-    sig, r, W, V, ref = _compare(p, blocks, 200, p.ns, p.nt)
+    sig, r, W, V, ref = _compare(p, blocks, 200, p.ns, p.nt, fp64_gemm=fp64_gemm)
     # directions with sigma ~ 1e-14 sigma_1 sit at the eps_sv cut: their count
     # is decided by rounding and may differ by one or two
     assert abs(r - len(ref["sigma"])) <= 2
