@@ -12,9 +12,9 @@
 // the digit products d_s d_t 2^(-7(s+t+2)); the pairs with s + t <= 7 are
 // kept (the dropped ones weigh below 2^-55 of the scales' product).  All
 // pairs of one diagonal D = s + t share a power of two, so one FP32
-// accumulator in tensor memory per diagonal sums them over a K chunk of 448:
-// every term is an integer of magnitude <= 2^12, a diagonal has at most 8
-// pairs, and 8 * 2^12 * 448 < 2^24, so every partial sum is an integer below
+// accumulator in tensor memory per diagonal sums them over a K chunk of at
+// most 448: every term is an integer of magnitude <= 2^12, a diagonal has at
+// most 8 pairs, and 8 * 2^12 * 448 < 2^24, so every partial sum is an integer below
 // 2^24 in magnitude that FP32 holds exactly, in whatever order the tensor
 // core adds.  The epilogue turns the eight exact sums into two 64-bit integers and
 // scales them into FP64; the chunks of a long K are added in FP64 in a fixed

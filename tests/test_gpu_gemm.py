@@ -55,9 +55,10 @@ MODES = [0, 1]  # ST_DGEMM_SIMT, ST_DGEMM_OZAKI
 TRANS = [(False, False), (True, False), (False, True), (True, True)]
 
 
-# (M, N, K, bits): ragged against the 128 x 64 tiles and the 256-long K
-# chunks; fewer rows or columns than one tile (TMA boxes past the last row);
-# K shorter than one 64-wide stage; K of the spatial dimension (192 chunks)
+# (M, N, K, bits): ragged against the 128 x 64 tiles and the K chunks (whole
+# 64-wide stages, at most 448, chosen per product to fill the SMs); fewer
+# rows or columns than one tile (TMA boxes past the last row); K shorter than
+# one stage; K of the spatial dimension (128 chunks of 384)
 SHAPES = [(200, 70, 600, 20), (5, 64, 49152, 15), (3000, 64, 20, 20), (130, 3, 20000, 15)]
 
 
@@ -101,7 +102,7 @@ def test_gemm_random_accuracy(mode, ta, tb):
 @pytest.mark.parametrize("shape", ["projection", "update"])
 def test_gemm_pod_shapes_full_size(shape):
     # the two products of a block Gram-Schmidt pass at the 2-D S4 transport
-    # size: L = W^T U (K = N = 49,152, K split in 192 chunks) and U -= W L
+    # size: L = W^T U (K = N = 49,152, split in 128 chunks of 384) and U -= W L
     rng = np.random.default_rng(3)
     N, r, b = 49152, 256, 64
     W = np.linalg.qr(rng.standard_normal((N, r)))[0]
