@@ -31,6 +31,16 @@ in column i + ns*j; Phi_s is N x ns.
   by LAPACK partial-pivot LU (numpy.linalg.solve).
 * ``reconstruct``      -- u^st ~= Phi_st uhat (Eq. ststateapproximation), by
   blocks: u^k = sum_{i,j} uhat_{ij} phi_t^{i,j}[k] phi_s^i.
+* ``spatial_march``    -- the spatial Galerkin ROM of Sec. 3.1 (Eq. galerkin)
+  marched by backward Euler (Eq. space_reduced_discretized_ODE) with the
+  reference state 0: (I - dt_k Ahat) uhat^k = uhat^{k-1} + dt_k Bhat f^k,
+  uhat^0 = Phi_s^T u0, one LAPACK solve per step.
+* ``fom_residual``     -- r^k(u^k, u^{k-1}) = u^k - u^{k-1} - dt_k A u^k -
+  dt_k B f^k (Eq. residual) for every step of a trajectory.
+* ``spatial_error_bound`` -- the residual-based bound of Theorem 1,
+  ||u^k - u~^k|| <= sum_{i<=k} (prod_{j=i..k} xi_j) ||r^i||, with
+  xi_j = ||(I - dt_j A)^-1||_2, plus the term (prod_{j<=k} xi_j) ||u^0 - u~^0||
+  that the one-step bound (Eq. one-timestep-bound) carries when u~^0 != u^0.
 """
 from __future__ import annotations
 
@@ -157,6 +167,10 @@ class ReducedModel:
         self.G, self.M, self.S = temporal_products(T, ns, nt, prob.dt)
         self.fhat = st_rhs(Phi_s, T, prob.B, prob.F, prob.dt, ns, nt)
         self.u0hat = st_initial(Phi_s, T, prob.u0, ns, nt)
+        # spatial ROM operators (Eq. galerkin): Bhat, uhat0 = Phi_s^T u0
+        self.Bhat = Phi_s.T @ prob.B
+        self.u0s = np.zeros(ns) if prob.u0 is None else Phi_s.T @ prob.u0
+        self.dt, self.F = prob.dt, prob.F
 
     def Ahat(self, theta: np.ndarray) -> np.ndarray:
         return np.tensordot(theta, self.Ahat_q, axes=(0, 0))
@@ -174,6 +188,12 @@ class ReducedModel:
               nt_m: Optional[int] = None) -> np.ndarray:
         A, f = self.operator(theta, ns_m, nt_m)
         return np.linalg.solve(A, f)
+
+    def spatial_march(self, theta: np.ndarray, ns_m: Optional[int] = None) -> np.ndarray:
+        """Spatial-ROM trajectory (ns_m x Nt) on the leading ns_m modes."""
+        ns_m = self.ns if ns_m is None else ns_m
+        return spatial_march(self.Ahat(theta)[:ns_m, :ns_m], self.Bhat[:ns_m], self.F, self.dt,
+                             self.u0s[:ns_m])
 
     def reconstruct(self, uhat: np.ndarray, ns_m: Optional[int] = None,
                     nt_m: Optional[int] = None) -> np.ndarray:
@@ -201,3 +221,44 @@ def rel_error(U_ref: np.ndarray, U: np.ndarray) -> float:
 def st_inf_norm(U: np.ndarray) -> float:
     """Space-time infinity norm max_k ||u^k||_2 (Eq. spacetimeinfnorm)."""
     return float(np.max(np.linalg.norm(U, axis=0)))
+
+
+def spatial_march(Ahat_mu: np.ndarray, Bhat: np.ndarray, F: np.ndarray, dt: np.ndarray,
+                  uhat0: Optional[np.ndarray] = None) -> np.ndarray:
+    """Backward-Euler march of the spatial ROM (Eq. space_reduced_discretized_ODE,
+    reference state 0).  Returns Uhat (ns x Nt) whose column k-1 is uhat^k."""
+    ns = Ahat_mu.shape[0]
+    u = np.zeros(ns) if uhat0 is None else np.array(uhat0, dtype=np.float64)
+    out = np.empty((ns, dt.shape[0]))
+    for k in range(dt.shape[0]):
+        u = np.linalg.solve(np.eye(ns) - dt[k] * Ahat_mu, u + dt[k] * (Bhat @ F[k]))
+        out[:, k] = u
+    return out
+
+
+def fom_residual(A, dt: np.ndarray, B: np.ndarray, F: np.ndarray, U: np.ndarray,
+                 u_init: np.ndarray) -> np.ndarray:
+    """Columns r^k(u^k, u^{k-1}) (Eq. residual) of a trajectory U (N x Nt)
+    started from u_init."""
+    R = np.empty_like(U)
+    prev = u_init
+    for k in range(dt.shape[0]):
+        R[:, k] = U[:, k] - prev - dt[k] * (A @ U[:, k]) - dt[k] * (B @ F[k])
+        prev = U[:, k]
+    return R
+
+
+def spatial_error_bound(A, dt: np.ndarray, R: np.ndarray, e0: float = 0.0) -> np.ndarray:
+    """Right-hand side of Theorem 1 at every step k = 1..Nt for residual
+    columns R (N x Nt); xi_j from the dense SVD of I - dt_j A (small cases)."""
+    n = A.shape[0]
+    Ad = A.toarray() if sp.issparse(A) else np.asarray(A)
+    xi = np.array([1.0 / np.linalg.svd(np.eye(n) - h * Ad, compute_uv=False).min() for h in dt])
+    rn = np.linalg.norm(R, axis=0)
+    out = np.empty(dt.shape[0])
+    for k in range(dt.shape[0]):
+        b = np.prod(xi[:k + 1]) * e0
+        for i in range(k + 1):
+            b += np.prod(xi[i:k + 1]) * rn[i]
+        out[k] = b
+    return out

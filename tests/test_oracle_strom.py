@@ -1,7 +1,9 @@
-"""Pins of the oracle's space-time reduced operators (Secs. 3.2, 4.3, 5.2)."""
+"""Pins of the oracle's reduced models: space-time (Secs. 3.2, 4.3, 5.2) and
+spatial (Secs. 3.1, 5.1)."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
+import scipy.sparse as sp
 
 from oracle import fom, pod, strom
 from workloads import make_problem
@@ -124,3 +126,119 @@ def test_theorem3_error_bound(tiny):
         lhs = strom.st_inf_norm(Uf - Ur)
         bound = np.sqrt(p.Nt) / smin * strom.st_inf_norm(res)
         assert lhs <= bound * (1 + 1e-12)
+
+
+# ---- spatial Galerkin ROM (Sec. 3.1) and its error bound (Theorem 1) ----------
+
+def _ragged_dt(p):
+    # non-uniform steps, so that a step index off by one changes the result
+    return p.dt * (1.0 + 0.5 * np.sin(np.arange(p.Nt) + 1.0))
+
+
+def test_spatial_rom_full_basis_reproduces_fom(tiny):
+    # a square orthogonal Phi_s makes Eq. space_reduced_discretized_ODE the
+    # FOM (Eq. fom) in another basis, at any step sizes
+    p, blocks, r = tiny
+    rng = np.random.default_rng(4)
+    Phi = np.linalg.qr(np.concatenate([r["Phi_s"], rng.standard_normal((p.N, p.N - p.ns))], 1))[0]
+    Ahat_q = strom.spatial_reduced(p.rowptr, p.col, p.vals, Phi)
+    dt = _ragged_dt(p)
+    for mu in p.test_mu[:2]:
+        th = p.theta(mu)
+        A = fom.affine_operator(p.rowptr, p.col, p.vals, th)
+        Uf = fom.fom_march(A, dt, p.B, p.F, p.u0, solver="dense")
+        Uh = strom.spatial_march(np.tensordot(th, Ahat_q, axes=(0, 0)), Phi.T @ p.B, p.F, dt,
+                                 Phi.T @ p.u0)
+        assert strom.rel_error(Uf, Phi @ Uh) < 1e-12
+
+
+def test_spatial_rom_residual_orthogonal_to_basis(tiny):
+    # the ROM state u~^k = Phi_s uhat^k leaves a full-order residual (Eq.
+    # residual) that is nonzero but orthogonal to range(Phi_s) (Eq. approxres)
+    p, blocks, r = tiny
+    Phi = r["Phi_s"]
+    Ahat_q = strom.spatial_reduced(p.rowptr, p.col, p.vals, Phi)
+    dt = _ragged_dt(p)
+    for mu in p.test_mu[:3]:
+        th = p.theta(mu)
+        A = fom.affine_operator(p.rowptr, p.col, p.vals, th)
+        Uh = strom.spatial_march(np.tensordot(th, Ahat_q, axes=(0, 0)), Phi.T @ p.B, p.F, dt,
+                                 Phi.T @ p.u0)
+        Ut = Phi @ Uh
+        R = strom.fom_residual(A, dt, p.B, p.F, Ut, Phi @ (Phi.T @ p.u0))
+        scale = np.abs(Ut).max()
+        assert np.abs(R).max() > 1e-6 * scale
+        assert np.abs(Phi.T @ R).max() < 1e-13 * scale
+
+
+def test_spatial_rom_equals_spacetime_rom_with_complete_temporal_bases(tiny):
+    # with every Phi_t^i completed to an Nt x Nt orthogonal matrix, range(Phi_st)
+    # = range(I_Nt (x) Phi_s): the space-time Galerkin solution (Eq.
+    # st-galerkin) is then the spatial ROM trajectory, also for nested ns
+    p, blocks, r = tiny
+    ns, Nt = p.ns, p.Nt
+    rng = np.random.default_rng(5)
+    T = np.zeros((Nt, ns * Nt))
+    for i in range(ns):
+        seed = r["T"][:, [i + ns * j for j in range(p.nt)]]
+        Ti = np.linalg.qr(np.concatenate([seed, rng.standard_normal((Nt, Nt - p.nt))], 1))[0]
+        for j in range(Nt):
+            T[:, i + ns * j] = Ti[:, j]
+    rm = strom.ReducedModel(p, r["Phi_s"], T, ns, Nt)
+    for mu in p.test_mu[:3]:
+        th = p.theta(mu)
+        for ns_m in (ns, 2):
+            Ust = rm.reconstruct(rm.solve(th, ns_m, Nt), ns_m, Nt)
+            Usp = r["Phi_s"][:, :ns_m] @ rm.spatial_march(th, ns_m)
+            assert strom.rel_error(Usp, Ust) < 1e-12
+
+
+def test_theorem1_error_bound(tiny):
+    # ||u^k - u~^k|| <= sum_{i<=k} prod_{j=i..k} xi_j ||r^i|| (Theorem 1), from
+    # the one-step identity e^k = (I - dt_k A)^-1 (e^{k-1} - r^k) (Eq. rearrange)
+    p, blocks, r = tiny
+    rm = strom.ReducedModel(p, r["Phi_s"], r["T"], p.ns, p.nt)
+    Phi = r["Phi_s"]
+    for mu in p.test_mu:
+        th = p.theta(mu)
+        A = fom.affine_operator(p.rowptr, p.col, p.vals, th)
+        Uf = fom.fom_march(A, p.dt, p.B, p.F, p.u0, solver="dense")
+        Ut = Phi @ rm.spatial_march(th)
+        ut0 = Phi @ rm.u0s
+        R = strom.fom_residual(A, p.dt, p.B, p.F, Ut, ut0)
+        E = Uf - Ut
+        e = p.u0 - ut0
+        scale = np.abs(Uf).max()
+        for k in range(p.Nt):
+            step = np.linalg.solve(np.eye(p.N) - p.dt[k] * A.toarray(), e - R[:, k])
+            assert np.abs(E[:, k] - step).max() < 1e-12 * scale
+            e = E[:, k]
+        bound = strom.spatial_error_bound(A, p.dt, R, float(np.linalg.norm(p.u0 - ut0)))
+        err = np.linalg.norm(E, axis=0)
+        assert err.max() > 1e-8 * scale
+        assert (err <= bound * (1 + 1e-12)).all()
+
+
+def test_theorem1_bound_is_attained_for_aligned_scalar_errors():
+    # N = 1, A = a < 0: xi_k = 1 / (1 - dt_k a) > 0 and e^k = xi_k (e^{k-1} -
+    # r^k).  With e^0 >= 0 and every r^k <= 0 no term cancels, so the triangle
+    # inequalities of the proof are equalities and the bound equals |e^k|.
+    a = -2.0
+    dt = np.array([0.1, 0.3, 0.05, 0.2, 0.15])
+    A = np.array([[a]])
+    B = np.array([[1.0]])
+    F = np.array([[1.0], [0.5], [-2.0], [0.0], [3.0]])
+    u0 = np.array([0.7])
+    U = fom.fom_march(sp.csr_matrix(A), dt, B, F, u0, solver="dense")
+    c = np.array([0.3, 0.01, 0.2, 0.05, 0.4])   # r^k = -c_k
+    e0 = 0.25
+    E = np.empty(len(dt))
+    e = e0
+    for k in range(len(dt)):
+        e = (e + c[k]) / (1.0 - dt[k] * a)
+        E[k] = e
+    Ut = U - E[None, :]
+    R = strom.fom_residual(A, dt, B, F, Ut, u0 - e0)
+    assert np.abs(R[0] + c).max() < 1e-14
+    bound = strom.spatial_error_bound(A, dt, R, e0)
+    assert np.abs(bound - E).max() < 1e-14 * E.max()
