@@ -479,6 +479,25 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     uhat.copy_(step_uhat)
     m.st_sync()
 
+    # ---- spatial Galerkin ROM (Sec. 3.1) on the same batch: Nt dependent
+    # backward-Euler steps on the leading ns_p spatial modes per parameter
+    sp_u = torch.zeros((N_BATCH, Nt, ns), dtype=torch.float64, device=dev)
+    sp_status = torch.zeros(N_BATCH, dtype=torch.int32, device=dev)
+    ns_d = sz_d[:, 0].contiguous()
+    m.st_rom_spatial_march(N_BATCH, th_d, ns_d, sp_u, sp_status)
+    torch.cuda.synchronize()
+    o0 = torch.cuda.Event(enable_timing=True)
+    o1 = torch.cuda.Event(enable_timing=True)
+    o0.record(stream)
+    for _ in range(args.steps):
+        m.st_rom_spatial_march(N_BATCH, th_d, ns_d, sp_u, sp_status)
+    o1.record(stream)
+    torch.cuda.synchronize()
+    m.st_sync()
+    sp_ms = o0.elapsed_time(o1) / args.steps
+    spatial = {"ms": sp_ms, "solves_per_s": N_BATCH / (sp_ms / 1e3),
+               "status_ok": int((sp_status == 0).sum()), "sizes": "ns_p of the batch, Nt steps each"}
+
     # ---- learned surrogate (c5): train on ROM solutions, gated inference --
     surrogate = None
     if not args.no_surrogate:
@@ -500,6 +519,18 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         err = float(torch.linalg.norm(fsn[j] - ur[j]) / torch.linalg.norm(fsn[j]))
         key = f"({sizes[k][0]},{sizes[k][1]})"
         acc[key] = max(acc.get(key, 0.0), err)
+    # the spatial ROM's error on the same parameters: u^k = Phi_s[:, :ns_p] uhat^k
+    phi = torch.empty((ns, N), dtype=torch.float64, device=dev)
+    m.st_model_get_basis(phi)
+    torch.cuda.synchronize()
+    sp_acc = {}
+    for k in sel:
+        a = int(sizes[k][0])
+        j = int(np.where(sel == k)[0][0])
+        us = sp_u[k, :, :a] @ phi[:a]
+        err = float(torch.linalg.norm(fsn[j] - us) / torch.linalg.norm(fsn[j]))
+        sp_acc[f"ns={a}"] = max(sp_acc.get(f"ns={a}", 0.0), err)
+    spatial["rel_err_vs_fom"] = sp_acc
 
     # ---- roofline of the dominant kernel ---------------------------------
     nnz = prob.nnz
@@ -555,6 +586,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                 "phases_ms": phases,
                 "online_solves_per_s": N_BATCH / ((phases["solve"] + phases["reconstruct"]) / 1e3),
                 "online_modes": online,
+                "spatial_rom": spatial,
                 "surrogate": surrogate,
                 "fom_mu_per_s": n_train / (phases["fom"] / 1e3),
                 "fom_bicgstab_iters_mean": float(iters.mean()),

@@ -302,6 +302,29 @@ st_status st_rom_reconstruct(st_model* m, int32_t n_mu, const double* uhat,
                              const int32_t* ns_nt, double* u, int32_t n_out, const double* Cout,
                              double* y);
 
+/* Batched spatial Galerkin ROM (Sec. 3.1, Eq. galerkin with reference state
+ * 0), the model the space-time ROM is compared with, marched by backward
+ * Euler (Eq. space_reduced_discretized_ODE) over the assembled steps:
+ *   (I - dt_k Ahat(mu)) uhat^k = uhat^{k-1} + dt_k Bhat f^k,  k = 1..Nt,
+ *   uhat^0 = Phi_s^T u0 (0 without u0),  Ahat(mu) = sum_q theta_q Ahat_q,
+ * with Bhat = Phi_s^T B and f^k the rows of F given to st_rom_assemble.
+ * Sample p uses the leading ns_p spatial modes.  The matrix of each run of
+ * equal steps is inverted once, by Gauss-Jordan elimination with partial
+ * pivoting in FP64; every step is then one matrix-vector product.
+ *   theta  dev [n_mu x Q] row major
+ *   ns_mu  dev [n_mu] (ns_p, 1 <= ns_p <= ns) or NULL for the model's ns
+ *   uhat   dev [n_mu x Nt x ns]: sample p writes uhat^k_i (i < ns_p) at
+ *          uhat[(p Nt + k - 1) ns + i]; entries i >= ns_p are left as they
+ *          are; after a singular matrix the remaining steps are NaN
+ *   status dev [n_mu] or NULL: ST_OK, ST_ERR_ARG (bad ns_p, nothing
+ *          written), ST_ERR_SINGULAR (a zero or non-finite pivot column),
+ *          ST_ERR_NONFINITE; any of these is also reported by st_sync
+ * Requires st_rom_assemble (ST_ERR_STATE otherwise); ST_ERR_ARG when the
+ * ns x ns matrix does not fit one block's shared memory (ns above ~160).
+ * Asynchronous, deterministic, no device allocation. */
+st_status st_rom_spatial_march(st_model* m, int32_t n_mu, const double* theta,
+                               const int32_t* ns_mu, double* uhat, int32_t* status);
+
 /* Learned surrogate mu -> uhat (no counterpart in the paper; it serves the
  * many-query use the paper motivates): a 3-layer MLP 2 -> 256 -> 256 -> ns*nt
  * with exact-erf GELU, FP32 master weights, BF16 copies on the tensor cores,

@@ -84,6 +84,7 @@ _SIGS = {
     "st_rom_solve": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_solve_static": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_reconstruct": (c_int32, [_P, c_int32, _P, _P, _P, c_int32, _P, _P]),
+    "st_rom_spatial_march": (c_int32, [_P, c_int32, _P, _P, _P, _P]),
     "st_rom_surrogate_train": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P, c_int32, c_int32, ctypes.c_float,
                                          ctypes.c_uint64, _P]),
     "st_rom_surrogate_infer": (c_int32, [_P, c_int32, _P, _P, c_double, _P, _P, _P, _P]),
@@ -275,6 +276,10 @@ class Model:
     def st_rom_reconstruct(self, n_mu, uhat, ns_nt, u=None, n_out=0, Cout=None, y=None) -> None:
         check(lib.st_rom_reconstruct(self.handle, n_mu, ptr(uhat), ptr(ns_nt), ptr(u), n_out,
                                      ptr(Cout), ptr(y)))
+
+    def st_rom_spatial_march(self, n_mu, theta, ns_mu, uhat, status=None) -> None:
+        check(lib.st_rom_spatial_march(self.handle, n_mu, ptr(theta), ptr(ns_mu), ptr(uhat),
+                                       ptr(status)))
 
 
 def _surrogate_methods():

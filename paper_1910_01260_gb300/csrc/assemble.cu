@@ -10,6 +10,7 @@
 //        M_i and S_i are the (i, i) diagonal blocks of G1 and G2.
 //   fhat^st[i + ns j] = sum_k dt_k T[k, i + ns j] (Phi_s^T B f^k)_i
 //   uhat0^st[i + ns j] = T[0, i + ns j] (Phi_s^T u0)_i
+// and, for the spatial ROM (Eq. galerkin), Bhat f^k per step and Phi_s^T u0.
 #include <algorithm>
 #include <vector>
 
@@ -92,6 +93,18 @@ __global__ void rhs_kernel(int ns, int nt, int Nt, int n_in, const double* __res
     }
 }
 
+// bs[i + ns k] = sum_s Bhat[i, s] F[k, s]: the spatial ROM's input term of step k + 1
+__global__ void spatial_forcing_kernel(int ns, int Nt, int n_in, const double* __restrict__ Bhat,
+                                       const double* __restrict__ F, double* bs) {
+    const int tot = ns * Nt;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+        const int i = t % ns, k = t / ns;
+        double g = 0.0;
+        for (int s = 0; s < n_in; ++s) g = fma(Bhat[i + (int64_t)s * ns], F[(int64_t)k * n_in + s], g);
+        bs[t] = g;
+    }
+}
+
 __global__ void to_f32_kernel(int64_t n, const double* __restrict__ x, float* y) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x)
@@ -123,6 +136,8 @@ extern "C" st_status st_rom_assemble(st_model* m, const double* dt, int32_t n_in
     ST_CUDA_TRY(cudaMalloc(&m->d_S, sizeof(double) * ns * nt * nt));
     ST_CUDA_TRY(cudaMalloc(&m->d_rhs, sizeof(double) * n));
     ST_CUDA_TRY(cudaMalloc(&m->d_dt, sizeof(double) * Nt));
+    ST_CUDA_TRY(cudaMalloc(&m->d_bs, sizeof(double) * ns * Nt));
+    ST_CUDA_TRY(cudaMalloc(&m->d_u0s, sizeof(double) * ns));
     // workspace: Y (Q x N x ns) | Td (Nt x n) | G1, G2 (n x n) | Bhat (ns x n_in) | u0hat (ns) | F (Nt x n_in)
     const size_t szY = (size_t)Q * N * ns, szTd = (size_t)Nt * n, szG = (size_t)n * n;
     const size_t szB = (size_t)ns * std::max(n_in, 1), szF = (size_t)Nt * std::max(n_in, 1);
@@ -170,6 +185,12 @@ extern "C" st_status st_rom_assemble(st_model* m, const double* dt, int32_t n_in
     rhs_kernel<<<gridn(m, n), 256, 0, st>>>(ns, nt, Nt, n_in, m->d_dt, m->d_T, Bhat, dF,
                                             u0 ? u0hat : nullptr, m->d_rhs);
     ST_TRY(st_check_launch("rhs"));
+    spatial_forcing_kernel<<<gridn(m, (int64_t)ns * Nt), 256, 0, st>>>(ns, Nt, n_in, Bhat, dF, m->d_bs);
+    ST_TRY(st_check_launch("spatial forcing"));
+    if (u0)
+        ST_CUDA_TRY(cudaMemcpyAsync(m->d_u0s, u0hat, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
+    else
+        ST_CUDA_TRY(cudaMemsetAsync(m->d_u0s, 0, sizeof(double) * ns, st));
     m->assembled = true;
     return ST_OK;
 }

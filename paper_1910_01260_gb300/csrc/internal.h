@@ -103,6 +103,8 @@ struct st_model {
     double* d_S = nullptr;     // ns x nt x nt
     double* d_rhs = nullptr;   // n: fhat^st + uhat0^st
     double* d_dt = nullptr;    // Nt
+    double* d_bs = nullptr;    // ns x Nt: Bhat f^k of the spatial ROM in column k-1
+    double* d_u0s = nullptr;   // ns: Phi_s^T u0 (zero without u0)
 
     // device error word and barrier counters
     int32_t* d_err = nullptr;

@@ -185,7 +185,10 @@ static void free_reduced(st_model* m) {
     cudaFree(m->d_S);
     cudaFree(m->d_rhs);
     cudaFree(m->d_dt);
+    cudaFree(m->d_bs);
+    cudaFree(m->d_u0s);
     m->d_Ahat = m->d_G = m->d_M = m->d_S = m->d_rhs = m->d_dt = nullptr;
+    m->d_bs = m->d_u0s = nullptr;
     m->d_G32 = nullptr;
     m->assembled = false;
 }
