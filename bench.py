@@ -495,8 +495,16 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     torch.cuda.synchronize()
     m.st_sync()
     sp_ms = o0.elapsed_time(o1) / args.steps
+    # FP64 flops per launch: per parameter one Gauss-Jordan inverse (2 n^3) of
+    # I - dt Ahat(mu) (2 Q n^2 to form) and Nt steps of 2 n^2 + 2 n
+    sp_n = sizes[:, 0].astype(np.float64)
+    sp_flops = float(np.sum(Nt * (2.0 * sp_n ** 2 + 2.0 * sp_n) + 2.0 * sp_n ** 3 +
+                            2.0 * theta_b.shape[1] * sp_n ** 2))
+    sp_tf = sp_flops / (sp_ms * 1e-3) / 1e12
     spatial = {"ms": sp_ms, "solves_per_s": N_BATCH / (sp_ms / 1e3),
-               "status_ok": int((sp_status == 0).sum()), "sizes": "ns_p of the batch, Nt steps each"}
+               "status_ok": int((sp_status == 0).sum()), "sizes": "ns_p of the batch, Nt steps each",
+               "gflop_per_launch": sp_flops / 1e9, "achieved_tflops": sp_tf,
+               "frac_fp64": sp_tf / FP64_PEAK_TFLOPS}
 
     # ---- learned surrogate (c5): train on ROM solutions, gated inference --
     surrogate = None
@@ -609,6 +617,7 @@ def run_case(case: str) -> None:
     fom: FOM march of the 16 training parameters, 10 steps (one launch);
     pod: full-size snapshots, then the incremental POD;
     solve: seeded (40,12) bases, the 4096-parameter batch in FP64 and FP32-LU;
+    spatial: the same bases, the spatial-ROM march of that batch (its ns_p);
     mlp: surrogate forward (tcgen05 GEMMs) on 65,536 parameters;
     fomfull: the full 200-step march of the 16 training parameters, timed."""
     import torch
@@ -670,6 +679,13 @@ def run_case(case: str) -> None:
             m.st_rom_solve(N_BATCH, th, sz, uh)
             m.st_model_set_options(precision=st.ST_FP32_LU, refine_steps=3)
             m.st_rom_solve(N_BATCH, th, sz, uh)
+        elif case == "spatial":
+            mu, sizes = c4_batch(N_BATCH, prob)
+            th = torch.tensor(prob.theta(mu), device=dev)
+            ns_p = torch.tensor(sizes[:, 0].copy(), device=dev)
+            us = torch.zeros((N_BATCH, prob.Nt, prob.ns), dtype=torch.float64, device=dev)
+            m.st_rom_spatial_march(N_BATCH, th, ns_p, us)
+            m.st_rom_spatial_march(N_BATCH, th, ns_p, us)
         elif case == "mlp":
             mu_tr, mu_inf = c5_samples(2048, 65536, prob)
             th_tr = torch.tensor(prob.theta(mu_tr), device=dev)

@@ -321,7 +321,9 @@ st_status st_rom_reconstruct(st_model* m, int32_t n_mu, const double* uhat,
  *          ST_ERR_NONFINITE; any of these is also reported by st_sync
  * Requires st_rom_assemble (ST_ERR_STATE otherwise); ST_ERR_ARG when the
  * ns x ns matrix does not fit one block's shared memory (ns above ~160).
- * Asynchronous, deterministic, no device allocation. */
+ * Samples run largest ns_p first.  Asynchronous and deterministic (a
+ * sample's result does not depend on the batch); a workspace of
+ * 4 (ns + 1 + 2 n_mu) bytes grows on demand. */
 st_status st_rom_spatial_march(st_model* m, int32_t n_mu, const double* theta,
                                const int32_t* ns_mu, double* uhat, int32_t* status);
 

@@ -111,7 +111,7 @@ struct st_model {
     unsigned int* d_bar = nullptr;  // [4]: arrival count, generation, abort flag, queue head
 
     // scratch buffers (grown on demand, reused across calls)
-    DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_oz, ws_solve, ws_misc;
+    DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_oz, ws_solve, ws_misc, ws_srom;
     OzSlot oz_slot[kOzSlots];
 
     // learned surrogate mu -> uhat (3-layer MLP, FP32 masters, BF16 copies)

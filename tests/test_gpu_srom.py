@@ -101,6 +101,28 @@ def test_spatial_march_full_basis_reproduces_fom():
     m.close()
 
 
+def test_spatial_march_wide_basis():
+    # ns above the block's 128 threads: one part per row, rows strided
+    p = problem_for("c1")
+    ns = 130
+    Phi = np.linalg.qr(np.random.default_rng(12).standard_normal((p.N, ns)))[0]
+    T = np.zeros((p.Nt, ns))
+    T[0] = 1.0
+    m = _gpu_model(p, Phi, T, ns, 1)
+    Ahat_q = strom.spatial_reduced(p.rowptr, p.col, p.vals, Phi)
+    Bhat = Phi.T @ p.B
+    mus = p.test_mu[:3]
+    sizes = np.array([130, 129, 64], dtype=np.int32)
+    U, status = _march(m, p.theta(mus), sizes, p.Nt, ns)
+    assert (status == 0).all()
+    for k, mu in enumerate(mus):
+        a = sizes[k]
+        Ah = np.tensordot(p.theta(mu), Ahat_q, axes=(0, 0))[:a, :a]
+        want = strom.spatial_march(Ah, Bhat[:a], p.F, p.dt)
+        assert rel_max(U[k, :, :a].T, want) < 1e-11
+    m.close()
+
+
 def test_spatial_march_equals_spacetime_solve_with_complete_temporal_bases(c1_model):
     # with every Phi_t^i completed to Nt x Nt the space-time ROM (st_rom_solve)
     # and the spatial ROM give the same trajectory
