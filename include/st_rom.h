@@ -327,6 +327,27 @@ st_status st_rom_reconstruct(st_model* m, int32_t n_mu, const double* uhat,
 st_status st_rom_spatial_march(st_model* m, int32_t n_mu, const double* theta,
                                const int32_t* ns_mu, double* uhat, int32_t* status);
 
+/* Full-order residual norms of approximate trajectories (Eq. residual):
+ *   r^k = u^k - u^{k-1} - dt_k A(mu) u^k - dt_k B f^k,  k = 1..Nt,  u^0 = u0,
+ * the factor of the a posteriori error bounds that a trajectory determines:
+ *   ||u^k - u~^k|| <= sum_{i<=k} (prod_{j=i..k} xi_j) ||r^i||   (Theorem 1,
+ *                     xi_j = ||(I - dt_j A)^-1||_2, u~^0 = u^0),
+ *   max_k ||u^k - u~^k|| <= sqrt(Nt) ||(A^st)^-1||_2 max_k ||r^k||  (Theorem 3),
+ * for a ROM trajectory u~ (the fields of st_rom_reconstruct, or Phi_s uhat^k
+ * of st_rom_spatial_march) at the cost of one operator application per step.
+ * Needs only the operator (no basis).
+ *   theta host [n_mu x Q] row major; dt host [Nt], all > 0
+ *   u0    dev [N] or NULL for 0
+ *   B     dev [N x n_in] column major; F host [Nt x n_in] row major (n_in may be 0)
+ *   U     dev [n_mu x Nt x N]: u^k(mu_p) at U + (p Nt + k - 1) N, the
+ *         layout of st_fom_march's snapshots and st_rom_reconstruct's fields
+ *   rnorm dev [n_mu x Nt]: ||r^k(mu_p)||_2 at rnorm[p Nt + k - 1]
+ * Deterministic (fixed-order sums).  1 <= Nt <= 65535.  Asynchronous. */
+st_status st_rom_residual_norms(st_model* m, int32_t n_mu, const double* theta, int32_t Nt,
+                                const double* dt, const double* u0, int32_t n_in,
+                                const double* B, const double* F, const double* U,
+                                double* rnorm);
+
 /* Learned surrogate mu -> uhat (no counterpart in the paper; it serves the
  * many-query use the paper motivates): a 3-layer MLP 2 -> 256 -> 256 -> ns*nt
  * with exact-erf GELU, FP32 master weights, BF16 copies on the tensor cores,

@@ -85,6 +85,7 @@ _SIGS = {
     "st_rom_solve_static": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_reconstruct": (c_int32, [_P, c_int32, _P, _P, _P, c_int32, _P, _P]),
     "st_rom_spatial_march": (c_int32, [_P, c_int32, _P, _P, _P, _P]),
+    "st_rom_residual_norms": (c_int32, [_P, c_int32, _P, c_int32, _P, _P, c_int32, _P, _P, _P, _P]),
     "st_rom_surrogate_train": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P, c_int32, c_int32, ctypes.c_float,
                                          ctypes.c_uint64, _P]),
     "st_rom_surrogate_infer": (c_int32, [_P, c_int32, _P, _P, c_double, _P, _P, _P, _P]),
@@ -276,6 +277,15 @@ class Model:
     def st_rom_reconstruct(self, n_mu, uhat, ns_nt, u=None, n_out=0, Cout=None, y=None) -> None:
         check(lib.st_rom_reconstruct(self.handle, n_mu, ptr(uhat), ptr(ns_nt), ptr(u), n_out,
                                      ptr(Cout), ptr(y)))
+
+    def st_rom_residual_norms(self, theta, dt, u0, B, F, U, rnorm) -> None:
+        th = _host(theta, np.float64)
+        dth = _host(dt, np.float64)
+        Fh = _host(F, np.float64) if F is not None else None
+        n_in = 0 if Fh is None else (Fh.shape[1] if Fh.ndim == 2 else 1)
+        self._keep = [th, dth, Fh]
+        check(lib.st_rom_residual_norms(self.handle, th.shape[0], ptr(th), dth.shape[0], ptr(dth),
+                                        ptr(u0), n_in, ptr(B), ptr(Fh), ptr(U), ptr(rnorm)))
 
     def st_rom_spatial_march(self, n_mu, theta, ns_mu, uhat, status=None) -> None:
         check(lib.st_rom_spatial_march(self.handle, n_mu, ptr(theta), ptr(ns_mu), ptr(uhat),

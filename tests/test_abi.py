@@ -114,4 +114,5 @@ def test_null_handle_arguments(st):
     assert st.lib.st_pod_get_stats(None, None, None, 0, None) == st.ST_ERR_ARG
     assert st.lib.st_gemm_f64(None, 0, 0, 1, 1, 1, 1.0, None, 1, None, 1, 0.0, None, 1) == st.ST_ERR_ARG
     assert st.lib.st_rom_spatial_march(None, 1, None, None, None, None) == st.ST_ERR_ARG
+    assert st.lib.st_rom_residual_norms(None, 1, None, 1, None, None, 0, None, None, None, None) == st.ST_ERR_ARG
     st.lib.st_model_destroy(None)
