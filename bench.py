@@ -653,6 +653,7 @@ def run_case(case: str) -> None:
     pod: full-size snapshots, then the incremental POD;
     solve: seeded (40,12) bases, the 4096-parameter batch in FP64 and FP32-LU;
     spatial: the same bases, the spatial-ROM march of that batch (its ns_p);
+    residual: full-order residual norms of 4 seeded c4-size trajectories;
     mlp: surrogate forward (tcgen05 GEMMs) on 65,536 parameters;
     fomfull: the full 200-step march of the 16 training parameters, timed."""
     import torch
@@ -721,6 +722,14 @@ def run_case(case: str) -> None:
             us = torch.zeros((N_BATCH, prob.Nt, prob.ns), dtype=torch.float64, device=dev)
             m.st_rom_spatial_march(N_BATCH, th, ns_p, us)
             m.st_rom_spatial_march(N_BATCH, th, ns_p, us)
+        elif case == "residual":
+            g = torch.Generator(device=dev)
+            g.manual_seed(7)
+            mu, _ = c4_batch(4, prob)
+            Ut = torch.randn((4, prob.Nt, prob.N), dtype=torch.float64, device=dev, generator=g)
+            rn = torch.zeros((4, prob.Nt), dtype=torch.float64, device=dev)
+            m.st_rom_residual_norms(prob.theta(mu), prob.dt, None, B, prob.F, Ut, rn)
+            m.st_rom_residual_norms(prob.theta(mu), prob.dt, None, B, prob.F, Ut, rn)
         elif case == "mlp":
             mu_tr, mu_inf = c5_samples(2048, 65536, prob)
             th_tr = torch.tensor(prob.theta(mu_tr), device=dev)
