@@ -12,7 +12,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   i + ns*j holding phi_t^{i,j} (index order of Eq. spacetimebasis).
 * ``pod_block_incremental`` -- the incremental SVD of Sec. 4.2 (Eqs.
   factorization1 ... rankOneUpdateSVD2, Algorithms 1-2), taking one
-  parameter's Nt snapshots per update:
+  parameter's Nt snapshots per update (or any fixed number of consecutive
+  snapshot columns; one column per update is Algorithm 2's rank-one update):
     1. project the block on W: L1 = W^T U_p, E1 = U_p - W L1;
     2. within the block, column by column, project each column of E1 on the
        new directions found so far (two passes), and keep its normalised
@@ -155,11 +156,20 @@ def incremental_update(W: Optional[np.ndarray], sigma: Optional[np.ndarray],
 
 
 def pod_block_incremental(blocks: Sequence[np.ndarray], ns: int, nt: int, r_max: int,
-                          eps_svd: float = 1e-12, eps_sv: float = 1e-14) -> dict:
+                          eps_svd: float = 1e-12, eps_sv: float = 1e-14,
+                          cols_per_update: Optional[int] = None) -> dict:
     """Block form of the incremental POD of Sec. 4.2, then the temporal
-    bases of Eqs. incrementaltemporalsnapshotmat / temporalincrementalbasis."""
+    bases of Eqs. incrementaltemporalsnapshotmat / temporalincrementalbasis.
+    One update takes one parameter's Nt snapshots, or, with cols_per_update,
+    that many consecutive columns of U = [U_1 ... U_nmu]; cols_per_update = 1
+    streams the snapshots one at a time, the rank-one update of Algorithm 2."""
+    if cols_per_update is None:
+        parts = list(blocks)
+    else:
+        U = snapshot_matrix(blocks)
+        parts = [U[:, c:c + cols_per_update] for c in range(0, U.shape[1], cols_per_update)]
     W = s = V = None
-    for Up in blocks:
+    for Up in parts:
         W, s, V = incremental_update(W, s, V, Up, r_max, eps_svd, eps_sv)
     n_mu = len(blocks)
     Nt = blocks[0].shape[1]

@@ -1,4 +1,5 @@
-"""Pins of the oracle's POD (Sec. 4.1) and block-incremental SVD (Sec. 4.2)."""
+"""Pins of the oracle's POD (Sec. 4.1) and incremental SVD (Sec. 4.2): block
+updates and the rank-one streaming update of Algorithm 2."""
 import numpy as np
 import pytest
 
@@ -110,3 +111,48 @@ def test_canonical_signs():
     C = pod.canonical_signs(X)
     assert np.allclose(C[:, 0], -X[:, 0]) and np.allclose(C[:, 1], -X[:, 1])
     assert np.allclose(pod.canonical_signs(-X), C)
+
+
+# ---- the rank-one streaming update of Algorithm 2 (one snapshot per update) ----
+
+def test_rank_one_stream_equals_exact_when_untruncated(c1_blocks):
+    p, blocks = c1_blocks
+    ex = pod.pod_exact(blocks, p.ns, p.nt)
+    inc = pod.pod_block_incremental(blocks, p.ns, p.nt, r_max=10 ** 6, eps_svd=1e-14,
+                                    eps_sv=1e-15, cols_per_update=1)
+    k = 40
+    s0 = ex["sigma"][0]
+    assert np.abs(inc["sigma"][:k] - ex["sigma"][:k]).max() < 1e-12 * s0
+    assert np.abs(pod.canonical_signs(inc["Phi_s"]) - pod.canonical_signs(ex["Phi_s"])).max() < 1e-9
+    for i in range(p.ns):
+        cols = [i + p.ns * j for j in range(p.nt)]
+        Pe = ex["T"][:, cols] @ ex["T"][:, cols].T
+        Pi = inc["T"][:, cols] @ inc["T"][:, cols].T
+        assert np.abs(Pe - Pi).max() < 1e-8
+    # U = W Sigma V^T with V's rows in snapshot-column order (Eq. SVDsummation)
+    U = pod.snapshot_matrix(blocks)
+    assert np.abs(inc["W"] @ np.diag(inc["sigma"]) @ inc["V"].T - U).max() < 1e-11 * s0
+
+
+def test_rank_one_stream_on_a_hand_sized_case():
+    # three snapshots in R^3 with a dependent third one: after the rank-one
+    # updates the SVD is that of the 3 x 3 matrix, of rank 2
+    U = np.array([[3.0, 0.0, 6.0], [4.0, 0.0, 8.0], [0.0, 2.0, 0.0]])
+    inc = pod.pod_block_incremental([U], 1, 1, r_max=10, cols_per_update=1)
+    # columns u1 = (3,4,0), u2 = (0,0,2), u3 = 2 u1: U^T U = diag-free Gram of
+    # rank 2 with singular values sqrt(25 + 100) = sqrt(125) and 2
+    assert inc["W"].shape[1] == 2
+    assert np.allclose(inc["sigma"], [np.sqrt(125.0), 2.0], rtol=0, atol=1e-14)
+    assert np.abs(inc["W"] @ np.diag(inc["sigma"]) @ inc["V"].T - U).max() < 1e-14
+
+
+def test_rank_one_stream_truncated_keeps_leading_modes(c1_blocks):
+    p, blocks = c1_blocks
+    ex = pod.pod_exact(blocks, p.ns, p.nt)
+    inc = pod.pod_block_incremental(blocks, p.ns, p.nt, r_max=60, cols_per_update=1)
+    assert inc["W"].shape[1] == 60
+    s0 = ex["sigma"][0]
+    assert np.abs(inc["sigma"][:8] - ex["sigma"][:8]).max() < 1e-9 * s0
+    U = pod.snapshot_matrix(blocks)
+    approx = inc["W"] @ np.diag(inc["sigma"]) @ inc["V"].T
+    assert np.linalg.norm(U - approx) < 1e-3 * np.linalg.norm(U)
