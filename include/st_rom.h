@@ -90,6 +90,9 @@ typedef struct {
                              columns; the paper streams one sample's
                              snapshots, 1)                                   (1)      */
     int32_t fp64_gemm;    /* ST_DGEMM_SIMT or ST_DGEMM_OZAKI            (ST_DGEMM_OZAKI)  */
+    int32_t pod_cols;     /* when > 0: consecutive snapshot columns per update
+                             instead of whole samples; 1 streams one snapshot
+                             per update, the rank-one update of Algorithm 2  (0)      */
 } st_options;
 
 /* Fill *opt with the defaults shown above. */

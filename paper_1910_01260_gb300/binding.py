@@ -46,7 +46,7 @@ class st_options(ctypes.Structure):
     _fields_ = [("tol", c_double), ("maxit", c_int32), ("eps_svd", c_double),
                 ("eps_sv", c_double), ("r_max", c_int32), ("precision", c_int32),
                 ("spin_limit", c_int64), ("refine_steps", c_int32), ("jacobi_sweeps", c_int32),
-                ("pod_block", c_int32), ("fp64_gemm", c_int32)]
+                ("pod_block", c_int32), ("fp64_gemm", c_int32), ("pod_cols", c_int32)]
 
 
 class st_affine_csr(ctypes.Structure):

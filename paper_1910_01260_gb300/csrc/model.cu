@@ -133,6 +133,7 @@ void st_options_default(st_options* o) {
     o->jacobi_sweeps = 40;
     o->pod_block = 1;
     o->fp64_gemm = ST_DGEMM_OZAKI;
+    o->pod_cols = 0;
 }
 
 const char* st_last_error(void) { return g_last_error.c_str(); }
@@ -158,7 +159,7 @@ const char* st_status_string(st_status s) {
 static bool options_valid(const st_options& o) {
     return (o.tol > 0) && o.maxit >= 1 && o.r_max >= 1 && (o.eps_svd >= 0) && (o.eps_sv >= 0) &&
            o.spin_limit >= 1 && o.refine_steps >= 0 && o.refine_steps <= 16 && o.jacobi_sweeps >= 1 &&
-           o.pod_block >= 1 && o.pod_block <= 64 &&
+           o.pod_block >= 1 && o.pod_block <= 64 && o.pod_cols >= 0 &&
            (o.fp64_gemm == ST_DGEMM_SIMT || o.fp64_gemm == ST_DGEMM_OZAKI) &&
            (o.precision == ST_FP64 || o.precision == ST_FP32_ASSEMBLY || o.precision == ST_FP32_LU);
 }

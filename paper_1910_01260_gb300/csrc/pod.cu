@@ -973,9 +973,13 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     if (n_mu > 64) return st_fail(ST_ERR_ARG, "st_rom_build_basis: at most 64 parameter samples");
     const int64_t N = m->N;
     const int rmax = (int)std::min<int64_t>(m->opt.r_max, N);
-    // one update takes the snapshots of pod_block parameter samples
+    // one update takes the snapshots of pod_block parameter samples, or
+    // pod_cols consecutive snapshot columns (1: the rank-one stream of
+    // Algorithm 2)
+    const int64_t ncols_all = (int64_t)n_mu * Nt;
     const int pb = std::min<int>(m->opt.pod_block, n_mu);
-    const int bmax = Nt * pb;  // widest block
+    const int bcols = m->opt.pod_cols > 0 ? (int)std::min<int64_t>(m->opt.pod_cols, ncols_all) : Nt * pb;
+    const int bmax = bcols;  // widest block
     const int cap = rmax + bmax;
     const int64_t ldv = (int64_t)n_mu * Nt;
     const int pdim = std::max(bmax, rmax);
@@ -1180,9 +1184,9 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         *k_total = k;
         return ST_OK;
     };
-    for (int p0 = 0; p0 < n_mu; p0 += pb) {
-        const int bw = Nt * std::min(pb, n_mu - p0);  // columns of this block
-        const double* Up = snapshots + (size_t)p0 * Nt * N;
+    for (int64_t c0 = 0; c0 < ncols_all; c0 += bcols) {
+        const int bw = (int)std::min<int64_t>(bcols, ncols_all - c0);  // columns of this block
+        const double* Up = snapshots + (size_t)c0 * N;
         {
             const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(64, N / 2048));
             ST_PROF(m, "colnorm_kernels");

@@ -44,9 +44,10 @@ def test_struct_layout_matches_c(st):
 #include <stddef.h>
 #include "st_rom.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(st_options), offsetof(st_options, maxit),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(st_options), offsetof(st_options, maxit),
          offsetof(st_options, eps_svd), offsetof(st_options, r_max), offsetof(st_options, spin_limit),
          offsetof(st_options, jacobi_sweeps), offsetof(st_options, pod_block), offsetof(st_options, fp64_gemm),
+         offsetof(st_options, pod_cols),
          sizeof(st_affine_csr), offsetof(st_affine_csr, col),
          offsetof(st_affine_csr, vals), offsetof(st_affine_csr, n_terms));
   return 0;
@@ -60,7 +61,8 @@ int main(void) {
         vals = list(map(int, subprocess.run([exe], capture_output=True, text=True).stdout.split()))
     o, a = st.binding.st_options, st.binding.st_affine_csr
     mine = [ctypes.sizeof(o), o.maxit.offset, o.eps_svd.offset, o.r_max.offset, o.spin_limit.offset,
-            o.jacobi_sweeps.offset, o.pod_block.offset, o.fp64_gemm.offset, ctypes.sizeof(a), a.col.offset, a.vals.offset,
+            o.jacobi_sweeps.offset, o.pod_block.offset, o.fp64_gemm.offset, o.pod_cols.offset, ctypes.sizeof(a),
+            a.col.offset, a.vals.offset,
             a.n_terms.offset]
     assert vals == mine
 
@@ -68,7 +70,7 @@ int main(void) {
 def test_defaults_and_names(st):
     o = st.options()
     assert o.tol == 1e-13 and o.maxit == 1000 and o.r_max == 256 and o.refine_steps == 1 and o.pod_block == 1
-    assert o.fp64_gemm == st.ST_DGEMM_OZAKI
+    assert o.fp64_gemm == st.ST_DGEMM_OZAKI and o.pod_cols == 0
     assert st.lib.st_status_string(st.ST_ERR_SINGULAR) == b"ST_ERR_SINGULAR"
     assert st.lib.st_status_string(99) == b"ST_ERR_UNKNOWN"
 

@@ -135,3 +135,38 @@ def test_pod_multi_sample_blocks(pod_block):
         cols = [i + p.ns * j for j in range(p.nt)]
         assert projector_dist(Tm[:, cols], T[:, cols]) < 1e-8
     m.close()
+
+
+@pytest.mark.parametrize("pod_cols,r_max", [(1, 200), (7, 120)])
+def test_pod_column_stream(pod_cols, r_max):
+    """Updates of pod_cols consecutive snapshot columns (1: the rank-one
+    stream of Algorithm 2, 200 updates; 7: blocks that straddle parameter
+    boundaries) against the oracle on the same column blocks."""
+    torch = __import__("torch")
+    p = problem_for("c1")
+    blocks = oracle_fom(p, p.train_mu)
+    Nt = blocks[0].shape[1]
+    m = make_model(p, r_max=r_max, pod_cols=pod_cols)
+    sig, r = m.st_rom_build_basis(len(blocks), Nt, _snap_tensor(blocks), p.ns, p.nt)
+    ref = pod.pod_block_incremental(blocks, p.ns, p.nt, r_max=r_max, cols_per_update=pod_cols)
+    assert len(m.st_pod_get_stats()[0]) == -(-len(blocks) * Nt // pod_cols)
+    s0 = ref["sigma"][0]
+    k = min(len(sig), len(ref["sigma"]), 40)
+    assert np.abs(sig[:k] - ref["sigma"][:k]).max() < 1e-10 * s0
+    phi = torch.zeros((p.ns, p.N), dtype=torch.float64, device="cuda:0")
+    Tg = torch.zeros((p.ns * p.nt, Nt), dtype=torch.float64, device="cuda:0")
+    m.st_model_get_basis(phi, Tg)
+    Phi, Tm = phi.cpu().numpy().T, Tg.cpu().numpy().T
+    assert np.abs(pod.canonical_signs(Phi) - pod.canonical_signs(ref["Phi_s"])).max() < 1e-8
+    for i in range(p.ns):
+        cols = [i + p.ns * j for j in range(p.nt)]
+        assert projector_dist(Tm[:, cols], ref["T"][:, cols]) < 1e-7
+    W = torch.zeros((r, p.N), dtype=torch.float64, device="cuda:0")
+    V = torch.zeros((r, len(blocks) * Nt), dtype=torch.float64, device="cuda:0")
+    m.st_pod_get_state(W, V)
+    Wm, Vm = W.cpu().numpy().T, V.cpu().numpy().T
+    assert np.abs(Wm.T @ Wm - np.eye(r)).max() < 1e-12
+    if r_max >= 200:   # untruncated: the factorisation reproduces U
+        U = np.concatenate(blocks, axis=1)
+        assert np.abs(Wm @ np.diag(sig) @ Vm.T - U).max() < 1e-10 * sig[0]
+    m.close()
