@@ -655,7 +655,9 @@ def run_case(case: str) -> None:
     spatial: the same bases, the spatial-ROM march of that batch (its ns_p);
     residual: full-order residual norms of 4 seeded c4-size trajectories;
     mlp: surrogate forward (tcgen05 GEMMs) on 65,536 parameters;
-    fomfull: the full 200-step march of the 16 training parameters, timed."""
+    fomfull: the full 200-step march of the 16 training parameters, timed;
+    podstream: full-size snapshots, the POD by blocks of 8 samples and by the
+    rank-one stream (one snapshot per update, 3200 updates), timed."""
     import torch
 
     import paper_1910_01260_gb300 as st
@@ -667,7 +669,7 @@ def run_case(case: str) -> None:
                  stream=stream.cuda_stream)
     B = torch.tensor(prob.B.T.copy(), device=dev)
     n_train = len(prob.train_mu)
-    if case in ("fom", "fomfull", "pod"):
+    if case in ("fom", "fomfull", "pod", "podstream"):
         Nt = 10 if case == "fom" else prob.Nt
         snaps = torch.empty((n_train, Nt, prob.N), dtype=torch.float64, device=dev)
         m.st_fom_march(prob.theta(prob.train_mu), prob.dt[:Nt], None, B, prob.F[:Nt], snaps)
@@ -681,6 +683,25 @@ def run_case(case: str) -> None:
             m.st_sync()
             print(json.dumps({"fom_ms": t0.elapsed_time(t1), "iters_mean": float(iters.float().mean()),
                               "snap_checksum": float(snaps.abs().sum())}))
+        if case == "podstream":
+            out = {}
+            for name, cols in (("blocks_of_8_samples", 0), ("rank_one_stream", 1)):
+                m.st_model_set_options(pod_cols=cols)
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(stream)
+                sig, rank = m.st_rom_build_basis(n_train, Nt, snaps, prob.ns, prob.nt)
+                t1.record(stream)
+                m.st_sync()
+                out[name] = {"ms": t0.elapsed_time(t1), "rank": rank, "updates": len(m.st_pod_get_stats()[0]),
+                             "sigma": sig}
+            a, b = out["blocks_of_8_samples"]["sigma"], out["rank_one_stream"]["sigma"]
+            k = min(len(a), len(b))
+            for v in out.values():
+                del v["sigma"]
+            out["max_sigma_diff_rel_sigma1_first_40"] = float(np.abs(a[:40] - b[:40]).max() / a[0])
+            out["max_sigma_diff_rel_sigma1_all_common"] = float(np.abs(a[:k] - b[:k]).max() / a[0])
+            print(json.dumps(out))
         if case == "pod":
             m.st_rom_build_basis(n_train, Nt, snaps, prob.ns, prob.nt)
             m.st_sync()
