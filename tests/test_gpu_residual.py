@@ -144,6 +144,29 @@ def test_theorem1_bound_holds_with_library_residuals():
     m.close()
 
 
+def test_theorem3_bound_holds_with_library_residuals():
+    # space-time ROM on a tiny problem: max_k ||u^k - u~^k|| <= sqrt(Nt)
+    # ||(A^st)^-1||_2 max_k ||r^k|| (Theorem 3) with the library's residuals
+    p = make_problem(dim=1, M=8, quad="gl4", Nt=6, g="sin", ns=3, nt=2)
+    blocks = oracle_fom(p, p.train_mu)
+    ref = pod.pod_exact(blocks, p.ns, p.nt)
+    m = make_model(p)
+    m.st_model_set_basis(p.ns, p.nt, p.Nt, dev_tensor(ref["Phi_s"].T.copy()), dev_tensor(ref["T"].T.copy()))
+    m.st_rom_assemble(p.dt, dev_B(p), p.F, None)
+    th = p.theta(p.test_mu)
+    U = _rom_fields(m, p, th)
+    got = _norms(m, p, th, U)
+    for k in range(len(th)):
+        A = fom.affine_operator(p.rowptr, p.col, p.vals, th[k])
+        Uf = fom.fom_march(A, p.dt, p.B, p.F, None, solver="dense")
+        Ast, _ = fom.st_fom_system(A, p.dt, p.B, p.F, None)
+        smin = np.linalg.svd(Ast.toarray(), compute_uv=False).min()
+        err = strom.st_inf_norm(Uf - U[k].T)
+        assert err > 1e-8 * np.abs(Uf).max()
+        assert err <= np.sqrt(p.Nt) / smin * got[k].max() * (1 + 1e-10)
+    m.close()
+
+
 def test_residual_norms_deterministic_and_independent_of_batching(c1_rom):
     p, ref = c1_rom
     m = make_model(p)
