@@ -1,5 +1,5 @@
-// Learned surrogate mu -> uhat with a residual gate (the benchmark spec's
-// learned-part pattern; the paper has no counterpart).
+// Learned surrogate mu -> uhat with a residual gate, for many-query use of
+// the reduced model (the paper has no counterpart).
 //
 // Network: x = affine map of mu onto [-1,1]^2 -> Z1 = x W1^T + b1 ->
 // H1 = gelu(Z1) -> Z2 = H1 W2^T + b2 -> H2 = gelu(Z2) -> Y = H2 W3^T + b3,
