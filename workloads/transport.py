@@ -310,8 +310,12 @@ def make_problem(name: str = "custom", dim: int = 1, M: int = 8, quad: str = "gl
                    test_mu=uniform_mu(n_test, lo, hi, 2), ns=ns, nt=nt)
 
 
-# Named workloads (the five benchmark configurations).  c4 and c5 reuse c2's
-# full-order model and training set with a basis built to (ns, nt) = (40, 12).
+# Named workloads: c1 a 1-D slab (64 cells, 8 Gauss directions, 50 steps, 2x2
+# training parameters); c2 2-D S4 transport on 64x64 cells (N = 49,152, 200
+# steps, 4x4 training parameters); c3 2-D S6 transport on 256x256 cells
+# (N = 1,572,864, 500 steps, 8x4 training parameters); c4 c2's full-order
+# model and training set with a basis built to (ns, nt) = (40, 12), for the
+# 4096-parameter online batch; c5 the same model, for the surrogate.
 CONFIGS: Dict[str, dict] = {
     "c1": dict(dim=1, M=64, quad="gl8", Nt=50, source="box", g="sin", mu_hi=(1.5, 0.9),
                train=(2, 2), n_test=8, ns=8, nt=4),
