@@ -782,7 +782,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=200)
-    ap.add_argument("--case", default=None, help="run one profiling workload: fom, fomfull, pod, solve, mlp")
+    ap.add_argument("--case", default=None, help="run one profiling workload: fom, fomfull, pod, podstream, solve, spatial, "
+                         "residual, mlp")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
