@@ -146,13 +146,23 @@ def incremental_update(W: Optional[np.ndarray], sigma: Optional[np.ndarray],
     if r > 0:
         Vn[:p_rows] = V @ Vb[:r]
     Vn[p_rows:] = Vb[r:]
-    if Wn.shape[1] > 1:
-        if abs(Wn[:, 0] @ Wn[:, -1]) > min(eps_svd, EPS * n):
-            Qf, Rf = np.linalg.qr(Wn)
-            # R with a positive diagonal keeps each column's orientation, so
-            # W Sigma V^T is unchanged up to the lost orthogonality
-            Wn = Qf * np.where(np.diag(Rf) < 0, -1.0, 1.0)
+    Wn, _ = orthogonality_check(Wn, eps_svd)
     return Wn, sb, Vn
+
+
+def orthogonality_check(W: np.ndarray, eps_svd: float) -> Tuple[np.ndarray, bool]:
+    """Step 6: the orthogonality test at the end of Algorithm 2, read with an
+    absolute value, |w_1^T w_r| > min(eps_svd, eps * N), and when it fires the
+    re-orthogonalisation W = Q R (LAPACK Householder QR), with the signs of
+    Q's columns chosen so that R has a positive diagonal: then column i of the
+    result is the normalised part of w_i orthogonal to w_1 .. w_{i-1}, so no
+    column changes orientation and W Sigma V^T moves only by the lost
+    orthogonality.  Returns (W, fired)."""
+    n, r = W.shape
+    if r < 2 or not abs(W[:, 0] @ W[:, -1]) > min(eps_svd, EPS * n):
+        return W, False
+    Qf, Rf = np.linalg.qr(W)
+    return Qf * np.where(np.diag(Rf) < 0, -1.0, 1.0), True
 
 
 def pod_block_incremental(blocks: Sequence[np.ndarray], ns: int, nt: int, r_max: int,

@@ -156,3 +156,74 @@ def test_rank_one_stream_truncated_keeps_leading_modes(c1_blocks):
     U = pod.snapshot_matrix(blocks)
     approx = inc["W"] @ np.diag(inc["sigma"]) @ inc["V"].T
     assert np.linalg.norm(U - approx) < 1e-3 * np.linalg.norm(U)
+
+
+# ---- the orthogonality check and re-orthogonalisation that end Algorithm 2 ----
+
+def _upper_perturbed_basis(n, r, delta, seed=3):
+    """W = Q0 R0 with Q0 orthonormal and R0 = I + delta * (strictly upper
+    triangular, entries in [1, 2)): by uniqueness of the QR factorisation with a
+    positive R diagonal, the re-orthogonalisation of W must return Q0 exactly
+    (to rounding), and w_1^T w_r = R0[0, r-1]."""
+    rng = np.random.default_rng(seed)
+    Q0 = np.linalg.qr(rng.standard_normal((n, r)))[0]
+    R0 = np.eye(r) + delta * np.triu(1.0 + rng.random((r, r)), 1)
+    return Q0, R0, Q0 @ R0
+
+
+@pytest.mark.parametrize("delta", [1e-6, -1e-6, 1e-9])
+def test_orthogonality_check_returns_the_positive_qr_factor(delta):
+    n, r = 300, 7
+    Q0, R0, W = _upper_perturbed_basis(n, r, delta)
+    assert abs(W[:, 0] @ W[:, -1] - R0[0, -1]) < 1e-15
+    Wq, fired = pod.orthogonality_check(W, eps_svd=1e-12)
+    # the test reads |w_1^T w_r|: a negative inner product fires as well
+    assert fired
+    # Q0 itself: a column with the wrong sign (R with a negative diagonal), a
+    # factor of W^T instead of W, or a skipped step all miss this by >= delta
+    assert np.abs(Wq - Q0).max() < 1e-14
+    assert np.abs(Wq.T @ Wq - np.eye(r)).max() < 1e-15 * n
+    # W = Wq R0: each column keeps its span with the earlier ones and its sign
+    assert np.abs(Wq.T @ W - R0).max() < 1e-14
+
+
+def test_orthogonality_check_threshold():
+    n, r = 300, 5
+    thr = min(1e-12, pod.EPS * n)               # 3.3e-14 at n = 300
+    Q0, R0, W = _upper_perturbed_basis(n, r, 0.0)
+    W[:, -1] += 0.5 * thr * W[:, 0]             # |w_1^T w_r| = thr / 2: no action
+    Wq, fired = pod.orthogonality_check(W, eps_svd=1e-12)
+    assert not fired and Wq is W
+    W[:, -1] += 2.0 * thr * W[:, 0]             # 2.5 thr: fires
+    assert pod.orthogonality_check(W, eps_svd=1e-12)[1]
+    # eps_svd below eps * N sets the threshold
+    W2 = Q0.copy()
+    W2[:, -1] += 1e-15 * W2[:, 0]
+    assert not pod.orthogonality_check(W2, eps_svd=1e-3)[1]
+    assert pod.orthogonality_check(W2, eps_svd=1e-16)[1]
+    # a single column is never tested
+    assert not pod.orthogonality_check(W[:, :1] * 3.0, eps_svd=0.0)[1]
+
+
+def test_incremental_update_reorthogonalises_a_drifted_basis(c1_blocks):
+    """A basis that has lost orthogonality (W = W0 (I + delta U), U strictly
+    upper triangular) enters an update: the update must end orthonormal, keep
+    each column's orientation, and still factorise the data up to O(delta)."""
+    p, blocks = c1_blocks
+    W0, s0, V0 = pod.incremental_update(None, None, None, blocks[0], 200, 1e-12, 1e-14)
+    r = W0.shape[1]
+    rng = np.random.default_rng(11)
+    delta = 1e-7
+    Wd = W0 @ (np.eye(r) + delta * np.triu(rng.random((r, r)), 1))
+    W_ref, s_ref, V_ref = pod.incremental_update(W0, s0, V0, blocks[1], 200, 1e-12, 1e-14)
+    W_d, s_d, V_d = pod.incremental_update(Wd, s0, V0, blocks[1], 200, 1e-12, 1e-14)
+    # without step 6 the drift of the input would survive at ~delta
+    assert np.abs(W_d.T @ W_d - np.eye(W_d.shape[1])).max() < 1e-13
+    k = min(10, W_d.shape[1])
+    # the leading directions keep their orientation (no sign flips)
+    assert np.all(np.einsum("ij,ij->j", W_d[:, :k], W_ref[:, :k]) > 0.99)
+    U = pod.snapshot_matrix(blocks[:2])
+    err = np.abs(W_d @ np.diag(s_d) @ V_d.T - U).max() / s_d[0]
+    assert err < 100 * delta
+    # the exact-arithmetic path does not fire on these snapshots
+    assert np.abs(W_ref.T @ W_ref - np.eye(W_ref.shape[1])).max() < 1e-13
