@@ -108,6 +108,15 @@ const char* st_status_string(st_status s);
  * models, all devices); a diagnostic counter, never reset. */
 int64_t st_kernel_launches(void);
 
+/* Measured FP64 fused multiply-add throughput of the current device
+ * (synchronous): blocks_per_sm x (SM count) blocks of 256 threads each run 8
+ * independent FMA chains of `iters` steps, timed with CUDA events after one
+ * shorter untimed launch.  *tflops = 2 * 8 * iters * threads / seconds / 1e12;
+ * ms (may be NULL) receives the timed launch's milliseconds.  The roofline
+ * denominator of the library's FP64-bound kernels.  ST_ERR_ARG for
+ * blocks_per_sm outside [1, 32], iters < 1 or a NULL tflops. */
+st_status st_probe_fp64_fma(int32_t blocks_per_sm, int64_t iters, double* tflops, double* ms);
+
 /* Create a model on the current CUDA device.  Converts the host CSR terms to
  * the library's sliced-ELL layout and uploads them (synchronous).
  * stream: a cudaStream_t (NULL = the legacy default stream); the model keeps
@@ -122,6 +131,9 @@ st_status st_model_create(const st_affine_csr* A, const st_options* opt, void* s
  * r_max changes take effect at the next st_rom_build_basis.  ST_ERR_ARG if
  * invalid (the old options stay). */
 st_status st_model_set_options(st_model* m, const st_options* opt);
+
+/* Copy the model's current options to *opt. */
+st_status st_model_get_options(st_model* m, st_options* opt);
 
 /* Release every resource of the model (synchronises its stream first). */
 void st_model_destroy(st_model* m);
@@ -217,6 +229,79 @@ st_status st_profile_read(st_model* m, int32_t cap, char* names, double* ms, int
 st_status st_pod_get_stats(st_model* m, int32_t* n_updates, int32_t* sweeps, int32_t cap,
                            int32_t* n_reorth);
 
+/* Resumable incremental SVD (Sec. 4.2, Algorithms 1-2).  The paper's
+ * incremental SVD exists to fold snapshots in as they are produced, without
+ * holding the whole snapshot matrix; these calls expose its state so a build
+ * can be continued later (with st_model_save/st_model_load in between) or fed
+ * group by group while the full-order march produces the next group.
+ * st_rom_build_basis is st_pod_reset + st_pod_update (all columns, updates of
+ * options.pod_block samples or options.pod_cols columns) + st_pod_finish.
+ *
+ * st_pod_reset: forget the state (r = 0, no columns consumed).
+ * st_pod_update (synchronous): fold the n_cols columns at snapshots (dev,
+ *   N x n_cols, column major) into the state, cols_per_update columns per
+ *   update (the last update may be narrower; 1 = the rank-one update of
+ *   Algorithm 2), with the truncation of options.eps_sv and options.r_max and
+ *   the dependence test of options.eps_svd (relative to each update's largest
+ *   column norm).  V gains n_cols rows.  ST_ERR_ARG for n_cols < 0 or
+ *   cols_per_update < 1; device errors of the update as for st_rom_build_basis.
+ * st_pod_finish (asynchronous after its checks): bases from the state,
+ *   Phi_s = W(:, 1:ns) (Eq. spatialincrementalbasis) and Phi_t^i from V read as
+ *   n_mu consecutive blocks of Nt rows (Eqs. incrementaltemporalsnapshotmat,
+ *   temporalincrementalbasis), replacing any basis and reduced operators.
+ *   Requires n_mu * Nt = columns consumed, ns <= r, nt <= min(Nt, n_mu);
+ *   ST_ERR_ARG otherwise.
+ * st_pod_set_state (synchronous): install a state: W dev [N x r], sigma host
+ *   [r] (finite, >= 0, non-increasing), V dev [rows x r] (rows = snapshot
+ *   columns the state stands for), all copied.  r = 0 clears W and sigma.
+ *   W need not be exactly orthonormal: the next update's orthogonality check
+ *   (end of Algorithm 2) re-orthogonalises it when |w_1^T w_r| exceeds
+ *   min(eps_svd, eps N).
+ * st_pod_get_dims: rank r and rows (columns consumed) of the state; either
+ *   pointer may be NULL. */
+st_status st_pod_reset(st_model* m);
+st_status st_pod_update(st_model* m, int64_t n_cols, const double* snapshots, int32_t cols_per_update);
+st_status st_pod_finish(st_model* m, int32_t n_mu, int32_t Nt, int32_t ns, int32_t nt);
+st_status st_pod_set_state(st_model* m, int32_t r, int64_t rows, const double* W, const double* sigma,
+                           const double* V);
+st_status st_pod_get_dims(st_model* m, int32_t* r, int64_t* rows);
+
+/* Persistence of a model (the offline stage's results, Secs. 4.2-4.3, for a
+ * later online stage or a resumed basis build).
+ * st_model_save (synchronous): writes the options, the affine operator, the
+ *   incremental-SVD state (W, sigma, V, per-update sweep counts and
+ *   re-orthogonalisations), the bases, the reduced operators and a trained
+ *   surrogate (parameters, Adam moments and step, output statistics,
+ *   parameter box) -- each part that exists -- to `path`, through a temporary
+ *   file renamed at the end.  ST_ERR_ARG if the file cannot be written.
+ * st_model_load (synchronous): creates a model on the current device with
+ *   `stream` (as st_model_create) from such a file and restores every saved
+ *   part; solves, reconstructions and surrogate inference then give the
+ *   saved model's results bit for bit, and st_pod_update continues the build.
+ *   ST_ERR_ARG for a missing, truncated or corrupt file (every section carries
+ *   a checksum), ST_ERR_OOM / ST_ERR_CUDA as st_model_create.
+ * st_model_file_info (host only, no GPU needed): validates a file as
+ *   st_model_load does and reports what it holds.
+ * File layout (little endian): "STROMMDL", u32 version 1, u32 section count,
+ * then per section char tag[4], u32 0, u64 payload bytes, payload, u64
+ * FNV-1a-64 of the payload; sections OPTS and OPER first, then any of PODS,
+ * BASE, REDU, SURR (payload layouts are listed in the library's io.cu). */
+typedef struct {
+    int32_t version;    /* file format version                                  */
+    int32_t n_terms;    /* Q                                                    */
+    int64_t n_rows;     /* N                                                    */
+    int64_t nnz;        /* stored entries of the operator pattern               */
+    int64_t pod_rows;   /* snapshot columns the incremental SVD has consumed    */
+    int32_t pod_rank;   /* r (0: no incremental-SVD state)                      */
+    int32_t ns, nt, Nt; /* basis sizes (0: no basis)                            */
+    int32_t assembled;  /* 1: reduced operators stored                          */
+    int32_t surrogate;  /* 1: trained surrogate stored                          */
+    int64_t n_params;   /* surrogate parameter count (0 without one)            */
+} st_model_info;
+st_status st_model_save(st_model* m, const char* path);
+st_status st_model_load(const char* path, void* stream, st_model** out);
+st_status st_model_file_info(const char* path, st_model_info* info);
+
 /* The FP64 matrix product of the incremental SVD and of the assembly
  * (Sec. 4.2: projections of snapshot blocks on the basis, W^T U and
  * U - W (W^T U), and the basis rotation), on the model's stream with the
@@ -281,11 +366,15 @@ st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta, const int
  * the library holds it until the process exits); the caller still passes the
  * inputs and outputs, and the call makes no cudaMalloc/cudaFree or other
  * allocating call.  Limit: 4*(2*n_mu + ns*nt + 17) bytes (rounded up to 256)
- * plus 8*(ns*nt)^2 bytes must fit in 32 MiB, else ST_ERR_ARG with a message;
- * when fewer than one block per SM fits, fewer blocks run (slower, same
- * results).  The first call on a device looks up that array's device address
- * (once per device, with the model's device current); make that first call
- * before any stream capture.  Every call uses the same array and zeroes what
+ * plus one factor matrix of (ns*nt)^2 entries (8 bytes each in the ST_FP64
+ * and ST_FP32_ASSEMBLY modes, 4 in ST_FP32_LU) must fit in 32 MiB, else
+ * ST_ERR_ARG with a message; the batch runs on as many blocks as matrices
+ * fit (at most the allocating path's count), so at large ns*nt fewer blocks
+ * run (slower, same results).  The first call on a device looks up that
+ * array's device address (once per device, with the model's device current)
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture, and do not keep using the library across a
+ * cudaDeviceReset of that device (the kept address would be stale).  Every call uses the same array and zeroes what
  * must start at zero: calls that overlap on the GPU (other streams, other
  * models on the same device) race and must be serialised by the caller. */
 st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double* theta,

@@ -23,4 +23,6 @@ from .binding import (  # noqa: F401
     lib,
     options,
     ptr,
+    st_model_file_info,
+    st_probe_fp64_fma,
 )

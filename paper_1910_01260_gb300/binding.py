@@ -49,6 +49,12 @@ class st_options(ctypes.Structure):
                 ("pod_block", c_int32), ("fp64_gemm", c_int32), ("pod_cols", c_int32)]
 
 
+class st_model_info(ctypes.Structure):
+    _fields_ = [("version", c_int32), ("n_terms", c_int32), ("n_rows", c_int64), ("nnz", c_int64),
+                ("pod_rows", c_int64), ("pod_rank", c_int32), ("ns", c_int32), ("nt", c_int32),
+                ("Nt", c_int32), ("assembled", c_int32), ("surrogate", c_int32), ("n_params", c_int64)]
+
+
 class st_affine_csr(ctypes.Structure):
     _fields_ = [("n_rows", c_int64), ("rowptr", POINTER(c_int64)), ("col", POINTER(c_int32)),
                 ("vals", POINTER(POINTER(c_double))), ("n_terms", c_int32)]
@@ -75,6 +81,16 @@ _SIGS = {
     "st_model_get_basis": (c_int32, [_P, _P, _P, _P]),
     "st_pod_get_state": (c_int32, [_P, _P, _P, _P, _P]),
     "st_pod_get_stats": (c_int32, [_P, _P, _P, c_int32, _P]),
+    "st_pod_reset": (c_int32, [_P]),
+    "st_pod_update": (c_int32, [_P, c_int64, _P, c_int32]),
+    "st_pod_finish": (c_int32, [_P, c_int32, c_int32, c_int32, c_int32]),
+    "st_pod_set_state": (c_int32, [_P, c_int32, c_int64, _P, _P, _P]),
+    "st_pod_get_dims": (c_int32, [_P, _P, _P]),
+    "st_model_get_options": (c_int32, [_P, POINTER(st_options)]),
+    "st_model_save": (c_int32, [_P, c_char_p]),
+    "st_model_load": (c_int32, [c_char_p, _P, POINTER(_P)]),
+    "st_model_file_info": (c_int32, [c_char_p, POINTER(st_model_info)]),
+    "st_probe_fp64_fma": (c_int32, [c_int32, c_int64, _P, _P]),
     "st_profile_enable": (c_int32, [_P, c_int32]),
     "st_profile_read": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_gemm_f64": (c_int32, [_P, c_int32, c_int32, c_int64, c_int64, c_int64, c_double, _P, c_int64, _P,
@@ -132,9 +148,39 @@ def options(**kw) -> st_options:
     return o
 
 
+def st_model_file_info(path) -> dict:
+    """Validate a saved model file on the host (no GPU) and report its contents."""
+    info = st_model_info()
+    check(lib.st_model_file_info(os.fsencode(path), ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in st_model_info._fields_}
+
+
+def st_probe_fp64_fma(blocks_per_sm=4, iters=20000):
+    """(TFLOP/s, ms) of the library's FP64 FMA throughput probe on the current device."""
+    tf = np.zeros(1, dtype=np.float64)
+    ms = np.zeros(1, dtype=np.float64)
+    check(lib.st_probe_fp64_fma(int(blocks_per_sm), int(iters), ptr(tf), ptr(ms)))
+    return float(tf[0]), float(ms[0])
+
+
 class Model:
     """Owner of one st_model handle; methods are the C entry points with the
     model argument bound.  Host inputs are converted to contiguous arrays."""
+
+    @classmethod
+    def st_model_load(cls, path, stream=None) -> "Model":
+        """A model restored from a file written by st_model_save."""
+        h = c_void_p()
+        st = stream if stream is None or isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
+        check(lib.st_model_load(os.fsencode(path), st, ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.handle = h
+        info = st_model_file_info(path)
+        self.N, self.Q = int(info["n_rows"]), int(info["n_terms"])
+        self.opts = st_options()
+        check(lib.st_model_get_options(h, ctypes.byref(self.opts)))
+        self._keep = []
+        return self
 
     def __init__(self, rowptr, col, vals, opts: st_options | None = None, stream=None):
         self._rowptr = _host(rowptr, np.int64)
@@ -222,6 +268,28 @@ class Model:
         ro = np.zeros(1, dtype=np.int32)
         check(lib.st_pod_get_stats(self.handle, ptr(n), ptr(sw), int(n[0]), ptr(ro)))
         return sw[:n[0]].tolist(), int(ro[0])
+
+    def st_pod_reset(self) -> None:
+        check(lib.st_pod_reset(self.handle))
+
+    def st_pod_update(self, n_cols, snapshots, cols_per_update) -> None:
+        check(lib.st_pod_update(self.handle, int(n_cols), ptr(snapshots), int(cols_per_update)))
+
+    def st_pod_finish(self, n_mu, Nt, ns, nt) -> None:
+        check(lib.st_pod_finish(self.handle, n_mu, Nt, ns, nt))
+
+    def st_pod_set_state(self, r, rows, W, sigma, V) -> None:
+        sig = _host(sigma, np.float64)
+        check(lib.st_pod_set_state(self.handle, int(r), int(rows), ptr(W), ptr(sig), ptr(V)))
+
+    def st_pod_get_dims(self):
+        r = np.zeros(1, dtype=np.int32)
+        rows = np.zeros(1, dtype=np.int64)
+        check(lib.st_pod_get_dims(self.handle, ptr(r), ptr(rows)))
+        return int(r[0]), int(rows[0])
+
+    def st_model_save(self, path) -> None:
+        check(lib.st_model_save(self.handle, os.fsencode(path)))
 
     def st_profile_enable(self, on: bool = True) -> None:
         check(lib.st_profile_enable(self.handle, 1 if on else 0))

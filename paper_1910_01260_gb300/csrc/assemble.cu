@@ -194,3 +194,25 @@ extern "C" st_status st_rom_assemble(st_model* m, const double* dt, int32_t n_in
     m->assembled = true;
     return ST_OK;
 }
+
+st_status st_internal_install_reduced(st_model* m, const double* Ahat, const double* G, const double* M,
+                                      const double* S, const double* rhs, const double* dt, const double* bs,
+                                      const double* u0s) {
+    if (!m->d_phi) return st_fail(ST_ERR_STATE, "reduced operators need a basis");
+    const size_t ns = m->ns, nt = m->nt, Nt = m->Nt, n = ns * nt, Q = m->Q;
+    cudaStream_t st = m->stream;
+    st_internal_free_reduced(m);
+    double** dst[8] = {&m->d_Ahat, &m->d_G, &m->d_M, &m->d_S, &m->d_rhs, &m->d_dt, &m->d_bs, &m->d_u0s};
+    const double* src[8] = {Ahat, G, M, S, rhs, dt, bs, u0s};
+    const size_t cnt[8] = {Q * ns * ns, n * n, ns * nt * nt, ns * nt * nt, n, Nt, ns * Nt, ns};
+    for (int i = 0; i < 8; ++i) {
+        ST_CUDA_TRY(cudaMalloc(dst[i], sizeof(double) * std::max<size_t>(cnt[i], 1)));
+        ST_CUDA_TRY(cudaMemcpyAsync(*dst[i], src[i], sizeof(double) * cnt[i], cudaMemcpyHostToDevice, st));
+    }
+    ST_CUDA_TRY(cudaMalloc(&m->d_G32, sizeof(float) * n * n));
+    to_f32_kernel<<<gridn(m, (int64_t)(n * n)), 256, 0, st>>>((int64_t)(n * n), m->d_G, m->d_G32);
+    ST_TRY(st_check_launch("to_f32"));
+    ST_CUDA_TRY(cudaStreamSynchronize(st));
+    m->assembled = true;
+    return ST_OK;
+}

@@ -54,6 +54,10 @@ struct st_model {
     st_options opt{};
     int num_sms = 0;
 
+    // affine operator terms as given (host CSR, kept for st_model_save)
+    std::vector<int64_t> h_rowptr;
+    std::vector<int32_t> h_col;
+    std::vector<double> h_vals;  // Q x nnz
     // affine operator terms in sliced-ELL form
     int64_t N = 0, nnz = 0;
     int Q = 0;
@@ -85,7 +89,8 @@ struct st_model {
 
     // incremental SVD state
     int pod_r = 0;
-    int64_t pod_rows = 0;
+    int64_t pod_rows = 0;  // snapshot columns consumed (rows of V)
+    int64_t pod_ldv = 0;   // leading dimension of V
     DevBuf W, V;
     std::vector<double> sigma;
     // per block update of the last basis build: middle-matrix Jacobi sweeps,
@@ -210,3 +215,14 @@ void st_internal_free_reduced(st_model* m);
 // st_rom_solve for those samples.
 st_status st_internal_solve_list(st_model* m, int n_list, const int* list, const double* theta,
                                  double* uhat, double* rel_res, int32_t* status);
+
+// Install reduced operators from host arrays (layouts of the "REDU" section
+// of a saved model; the FP32 copy of G is made on the device).
+st_status st_internal_install_reduced(st_model* m, const double* Ahat, const double* G, const double* M,
+                                      const double* S, const double* rhs, const double* dt, const double* bs,
+                                      const double* u0s);
+// Install a trained surrogate from host arrays (FP32 parameters and Adam
+// moments, FP64 output statistics, the parameter box, the Adam step count).
+st_status st_internal_mlp_install(st_model* m, int hidden, const float* params, const float* adam_m,
+                                  const float* adam_v, const double* mean, const double* stdv, const double* lo,
+                                  const double* hi, int64_t adam_t);

@@ -684,3 +684,25 @@ extern "C" st_status st_rom_surrogate_loss_grad(st_model* m, int32_t n, const do
     s.trained = false;
     return ST_OK;
 }
+
+st_status st_internal_mlp_install(st_model* m, int hidden, const float* params, const float* adam_m,
+                                  const float* adam_v, const double* mean, const double* stdv, const double* lo,
+                                  const double* hi, int64_t adam_t) {
+    auto& s = m->mlp;
+    if (hidden != s.hidden) return st_fail(ST_ERR_ARG, "saved surrogate: hidden width %d is not %d", hidden, s.hidden);
+    ST_TRY(setup(m, params, 0));
+    const size_t np = (size_t)s.n_params, no = (size_t)s.n_out;
+    ST_CUDA_TRY(cudaMemcpyAsync(s.adam_m.p, adam_m, sizeof(float) * np, cudaMemcpyHostToDevice, m->stream));
+    ST_CUDA_TRY(cudaMemcpyAsync(s.adam_v.p, adam_v, sizeof(float) * np, cudaMemcpyHostToDevice, m->stream));
+    ST_CUDA_TRY(cudaMemcpyAsync(s.stats.p, mean, sizeof(double) * no, cudaMemcpyHostToDevice, m->stream));
+    ST_CUDA_TRY(cudaMemcpyAsync((double*)s.stats.p + no, stdv, sizeof(double) * no, cudaMemcpyHostToDevice,
+                                m->stream));
+    ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    s.lo[0] = lo[0];
+    s.lo[1] = lo[1];
+    s.hi[0] = hi[0];
+    s.hi[1] = hi[1];
+    s.adam_t = adam_t;
+    s.trained = true;
+    return ST_OK;
+}

@@ -171,6 +171,12 @@ st_status st_model_set_options(st_model* m, const st_options* opt) {
     return ST_OK;
 }
 
+st_status st_model_get_options(st_model* m, st_options* opt) {
+    if (!m || !opt) return st_fail(ST_ERR_ARG, "st_model_get_options: NULL argument");
+    *opt = m->opt;
+    return ST_OK;
+}
+
 static void free_basis(st_model* m) {
     cudaFree(m->d_phi);
     cudaFree(m->d_T);
@@ -298,6 +304,16 @@ st_status st_model_create(const st_affine_csr* A, const st_options* opt, void* s
 
     st_model* m = new st_model();
     m->opt = o;
+    try {
+        m->h_rowptr.assign(A->rowptr, A->rowptr + N + 1);
+        m->h_col.assign(A->col, A->col + nnz);
+        m->h_vals.resize((size_t)A->n_terms * nnz);
+    } catch (...) {
+        delete m;
+        return st_fail(ST_ERR_OOM, "st_model_create: no host memory for the operator copy");
+    }
+    for (int q = 0; q < A->n_terms; ++q)
+        std::copy(A->vals[q], A->vals[q] + nnz, m->h_vals.begin() + (size_t)q * nnz);
     m->stream = (cudaStream_t)stream;
     m->N = N;
     m->nnz = nnz;
@@ -504,11 +520,19 @@ st_status st_pod_get_state(st_model* m, double* W, double* V, double* sigma, int
     if (W)
         ST_CUDA_TRY(cudaMemcpyAsync(W, m->W.p, sizeof(double) * m->N * m->pod_r,
                                     cudaMemcpyDeviceToDevice, m->stream));
-    if (V)
-        ST_CUDA_TRY(cudaMemcpyAsync(V, m->V.p, sizeof(double) * m->pod_rows * m->pod_r,
-                                    cudaMemcpyDeviceToDevice, m->stream));
+    if (V && m->pod_rows > 0)
+        ST_CUDA_TRY(cudaMemcpy2DAsync(V, sizeof(double) * m->pod_rows, m->V.p, sizeof(double) * m->pod_ldv,
+                                      sizeof(double) * m->pod_rows, m->pod_r, cudaMemcpyDeviceToDevice,
+                                      m->stream));
     if (sigma) std::memcpy(sigma, m->sigma.data(), sizeof(double) * m->pod_r);
     ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return ST_OK;
+}
+
+st_status st_pod_get_dims(st_model* m, int32_t* r, int64_t* rows) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_pod_get_dims: NULL model");
+    if (r) *r = m->pod_r;
+    if (rows) *rows = m->pod_rows;
     return ST_OK;
 }
 

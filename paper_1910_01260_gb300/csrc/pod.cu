@@ -963,40 +963,82 @@ int grid_for(st_model* m, int64_t n) {
 
 }  // namespace
 
-extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
-                                        const double* snapshots, int32_t ns, int32_t nt,
-                                        double* sigma_out, int32_t* rank_out) {
-    if (!m) return st_fail(ST_ERR_ARG, "st_rom_build_basis: NULL model");
-    if (!snapshots || n_mu < 1 || Nt < 1 || ns < 1 || nt < 1)
-        return st_fail(ST_ERR_ARG, "st_rom_build_basis: bad arguments");
-    if (nt > Nt || nt > n_mu) return st_fail(ST_ERR_ARG, "st_rom_build_basis: nt > min(Nt, n_mu)");
-    if (n_mu > 64) return st_fail(ST_ERR_ARG, "st_rom_build_basis: at most 64 parameter samples");
+namespace {
+
+// Grow buf to at least `bytes`, keeping its first keep_bytes (st_grow drops
+// the contents).
+st_status grow_keep(st_model* m, DevBuf& buf, size_t bytes, size_t keep_bytes) {
+    if (bytes <= buf.bytes) return ST_OK;
+    void* p = nullptr;
+    const size_t want = bytes + bytes / 8 + 256;
+    ST_CUDA_TRY(cudaMalloc(&p, want));
+    if (buf.p && keep_bytes)
+        ST_CUDA_TRY(cudaMemcpyAsync(p, buf.p, std::min(keep_bytes, buf.bytes), cudaMemcpyDeviceToDevice, m->stream));
+    if (buf.p) {
+        ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        ST_CUDA_TRY(cudaFree(buf.p));
+    }
+    buf.p = p;
+    buf.bytes = want;
+    return ST_OK;
+}
+
+// Make room for the state: W (N x wcols) keeping its r columns, and V with
+// a leading dimension of at least ldv_min rows and vcols columns, keeping its
+// pod_rows x r block.
+st_status pod_reserve(st_model* m, int wcols, int64_t ldv_min, int vcols) {
     const int64_t N = m->N;
-    const int rmax = (int)std::min<int64_t>(m->opt.r_max, N);
-    // one update takes the snapshots of pod_block parameter samples, or
-    // pod_cols consecutive snapshot columns (1: the rank-one stream of
-    // Algorithm 2)
-    const int64_t ncols_all = (int64_t)n_mu * Nt;
-    const int pb = std::min<int>(m->opt.pod_block, n_mu);
-    const int bcols = m->opt.pod_cols > 0 ? (int)std::min<int64_t>(m->opt.pod_cols, ncols_all) : Nt * pb;
-    const int bmax = bcols;  // widest block
-    const int cap = rmax + bmax;
-    const int64_t ldv = (int64_t)n_mu * Nt;
-    const int pdim = std::max(bmax, rmax);
-    cudaStream_t st = m->stream;
-    st_internal_free_basis(m);
+    const int r = m->pod_r;
+    ST_TRY(grow_keep(m, m->W, sizeof(double) * N * wcols, sizeof(double) * N * r));
+    if (m->pod_ldv >= ldv_min && m->V.bytes >= sizeof(double) * (size_t)m->pod_ldv * vcols) return ST_OK;
+    const int64_t ld = std::max(ldv_min, m->pod_ldv);
+    void* p = nullptr;
+    const size_t want = sizeof(double) * (size_t)ld * std::max(vcols, 1) + 256;
+    ST_CUDA_TRY(cudaMalloc(&p, want));
+    if (m->V.p && r > 0 && m->pod_rows > 0)
+        ST_CUDA_TRY(cudaMemcpy2DAsync(p, sizeof(double) * ld, m->V.p, sizeof(double) * m->pod_ldv,
+                                      sizeof(double) * m->pod_rows, r, cudaMemcpyDeviceToDevice, m->stream));
+    if (m->V.p) {
+        ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+        ST_CUDA_TRY(cudaFree(m->V.p));
+    }
+    m->V.p = p;
+    m->V.bytes = want;
+    m->pod_ldv = ld;
+    return ST_OK;
+}
+
+void pod_clear(st_model* m) {
     m->pod_r = 0;
     m->pod_rows = 0;
     m->sigma.clear();
     m->pod_sweeps.clear();
     m->pod_reorth = 0;
+}
+
+// Updates of the incremental SVD held by the model (W, sigma, V, r, rows)
+// with the ncols_all columns at `snapshots` (N x ncols_all, column major),
+// bcols columns per update (the last one may be narrower).
+st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshots, int bcols) {
+    const int64_t N = m->N;
+    int r = m->pod_r;
+    int64_t rows = m->pod_rows;
+    // rank cap; a state installed with more columns keeps them until the
+    // next truncation
+    const int rmax = (int)std::min<int64_t>(m->opt.r_max, N);
+    const int rcap = std::max(rmax, r);
+    bcols = (int)std::min<int64_t>(bcols, ncols_all);
+    const int bmax = bcols;  // widest block
+    const int cap = rcap + bmax;
+    ST_TRY(pod_reserve(m, cap, rows + ncols_all, rcap));
+    const int64_t ldv = m->pod_ldv;
+    const int pdim = std::max(bmax, rcap);
+    cudaStream_t st = m->stream;
     st_oz_invalidate(m);
 
     // buffers
-    ST_TRY(st_grow(m, m->W, sizeof(double) * N * cap));
-    ST_TRY(st_grow(m, m->V, sizeof(double) * ldv * rmax));
-    const size_t szW2 = (size_t)N * cap, szV2 = (size_t)ldv * rmax, szE = (size_t)N * bmax,
-                 szL = (size_t)rmax * bmax, szP = (size_t)pdim * pdim, szX = (size_t)cap * cap;
+    const size_t szW2 = (size_t)N * cap, szV2 = (size_t)ldv * rcap, szE = (size_t)N * bmax,
+                 szL = (size_t)rcap * bmax, szP = (size_t)pdim * pdim, szX = (size_t)cap * cap;
     int gs_blocks = 0;
     {
         int per_sm = 0;
@@ -1009,7 +1051,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     }
     const size_t szPart = std::max((size_t)2 * std::max(gs_blocks, 1) * (pdim + 2), (size_t)64 * bmax);
     const size_t szPan = (size_t)pdim * kGsPanel + 4 * (size_t)kGsPanel * kGsPanel;
-    const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 3 * szX + (size_t)cap * rmax * 2 +
+    const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 3 * szX + (size_t)cap * rcap * 2 +
                            szPart + pdim + 9 * cap + szPan + 32;
     ST_TRY(st_grow(m, m->ws_pod, sizeof(double) * doubles + sizeof(int) * (2 * cap + 16)));
     double* W2 = (double*)m->ws_pod.p;
@@ -1024,8 +1066,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
     double* Y = X + szX;
     double* Z = Y + szX;
     double* Ysel = Z + szX;
-    double* Vsel = Ysel + (size_t)cap * rmax;
-    double* partial = Vsel + (size_t)cap * rmax;
+    double* Vsel = Ysel + (size_t)cap * rcap;
+    double* partial = Vsel + (size_t)cap * rcap;
     // Gram-Schmidt panel workspace: H [pdim x panel] projections of a panel
     // on the earlier directions, G, R, Rinv, Pt [panel x panel]
     double* gsH = partial + szPart;
@@ -1103,9 +1145,10 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         st_count_launch();
         return ST_OK;
     };
-    int r = 0;
-    int64_t rows = 0;
     std::vector<double> h_sig;
+    // the singular values of the state on the device
+    if (r > 0)
+        ST_CUDA_TRY(cudaMemcpyAsync(d_sig, m->sigma.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
     auto read_k = [&](int* out) -> st_status {
         ST_CUDA_TRY(cudaMemcpyAsync(out, d_int, sizeof(int), cudaMemcpyDeviceToHost, st));
         ST_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1200,17 +1243,17 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         int k = 0;
         if (r > 0) {
             // first block pass: L = W^T U_p, E1 = U_p - W L, E1 = J1 P1
-            ST_TRY(st_dgemm_slot(m, 2, false, true, false, r, bw, N, 1.0, W, N, Up, N, 0.0, L, rmax));
-            ST_TRY(st_dgemm_slot(m, 3, false, false, false, N, bw, r, -1.0, W, N, L, rmax, 1.0, E, N));
+            ST_TRY(st_dgemm_slot(m, 2, false, true, false, r, bw, N, 1.0, W, N, Up, N, 0.0, L, rcap));
+            ST_TRY(st_dgemm_slot(m, 3, false, false, false, N, bw, r, -1.0, W, N, L, rcap, 1.0, E, N));
             int k1 = 0;
             ST_TRY(gs_block(E, bw, J, P1, bw, d_scalar, &k1));
             if (k1 > 0) {
                 // second block pass: L2 = W^T J1, E2 = J1 - W L2 = J P2 by Cholesky QR
                 // (E2 is orthonormal up to the rounding carried along W, so its
                 // Gram matrix is well conditioned); L += L2 P1, P = P2 P1
-                ST_TRY(st_dgemm_slot(m, 2, true, true, false, r, k1, N, 1.0, W, N, J, N, 0.0, L2, rmax));
+                ST_TRY(st_dgemm_slot(m, 2, true, true, false, r, k1, N, 1.0, W, N, J, N, 0.0, L2, rcap));
                 ST_CUDA_TRY(cudaMemcpyAsync(E, J, sizeof(double) * N * k1, cudaMemcpyDeviceToDevice, st));
-                ST_TRY(st_dgemm_slot(m, 3, true, false, false, N, k1, r, -1.0, W, N, L2, rmax, 1.0, E, N));
+                ST_TRY(st_dgemm_slot(m, 3, true, false, false, N, k1, r, -1.0, W, N, L2, rcap, 1.0, E, N));
                 ST_TRY(st_dgemm(m, true, false, k1, k1, N, 1.0, E, N, E, N, 0.0, Y, k1));
                 ST_CUDA_TRY(cudaMemsetAsync(d_int + 6, 0, sizeof(int), st));
                 {
@@ -1227,7 +1270,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
                 } else {
                     ST_TRY(gs_block(E, k1, J, P2, k1, nullptr, &k));
                 }
-                ST_TRY(st_dgemm(m, false, false, r, bw, k1, 1.0, L2, rmax, P1, bw, 1.0, L, rmax));
+                ST_TRY(st_dgemm(m, false, false, r, bw, k1, 1.0, L2, rcap, P1, bw, 1.0, L, rcap));
                 if (k > 0) ST_TRY(st_dgemm(m, false, false, k, bw, k1, 1.0, P2, k1, P1, bw, 0.0, P, bw));
             }
         } else {
@@ -1241,7 +1284,7 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         // middle matrix, transposed: X = Q^T (mrows x ncols); pivoted QR
         // X Pi = Q1 R, then one-sided Jacobi on Z = R^T with rotations
         // accumulated in Y:  Q = (Pi U_z) Sigma (Q1 Y)^T
-        build_qt_kernel<<<grid_for(m, (int64_t)mrows * ncols), 256, 0, st>>>(r, k, bw, d_sig, L, rmax, P, bw, X, cap);
+        build_qt_kernel<<<grid_for(m, (int64_t)mrows * ncols), 256, 0, st>>>(r, k, bw, d_sig, L, rcap, P, bw, X, cap);
         ST_TRY(st_check_launch("build_qt"));
         ST_TRY(run_qrp(mrows, ncols));
         build_rt_kernel<<<grid_for(m, (int64_t)ncols * ncols), 256, 0, st>>>(ncols, X, cap, d_piv, q_beta, Z, cap, Y, cap);
@@ -1317,6 +1360,8 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         // V2 = blkdiag(V, I) Vsel
         if (r > 0 && rows > 0)
             ST_TRY(st_dgemm(m, false, false, rows, rnew, r, 1.0, V, ldv, Vsel, cap, 0.0, V2, ldv));
+        else if (rows > 0)  // earlier columns added no direction: their rows of V are zero
+            ST_CUDA_TRY(cudaMemset2DAsync(V2, sizeof(double) * ldv, 0, sizeof(double) * rows, rnew, st));
         ST_CUDA_TRY(cudaMemcpy2DAsync(V2 + rows, sizeof(double) * ldv, Vsel + r, sizeof(double) * cap,
                                       sizeof(double) * bw, rnew, cudaMemcpyDeviceToDevice, st));
         ST_CUDA_TRY(cudaMemcpyAsync(W, W2, sizeof(double) * N * rnew, cudaMemcpyDeviceToDevice, st));
@@ -1352,27 +1397,110 @@ extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt,
         ST_CUDA_TRY(cudaStreamSynchronize(st));
     }
     m->pod_r = r;
-    m->pod_rows = ldv;
+    m->pod_rows = rows;
     m->sigma.assign(h_sig.begin(), h_sig.begin() + r);
-    if (rank_out) *rank_out = r;
-    if (sigma_out) for (int i = 0; i < r; ++i) sigma_out[i] = h_sig[i];
+    return ST_OK;
+}
+
+// Phi_s = W(:, 1:ns) and the temporal bases of the state's V read as n_mu
+// blocks of Nt rows (Eqs. spatialincrementalbasis, incrementaltemporalsnapshotmat,
+// temporalincrementalbasis).
+st_status pod_finish_impl(st_model* m, int n_mu, int Nt, int ns, int nt) {
+    const int64_t N = m->N;
+    const int r = m->pod_r;
+    cudaStream_t st = m->stream;
     if (ns > r) return st_fail(ST_ERR_ARG, "st_rom_build_basis: ns = %d exceeds the rank %d", ns, r);
-    // bases
+    if ((int64_t)n_mu * Nt != m->pod_rows)
+        return st_fail(ST_ERR_ARG, "st_pod_finish: n_mu * Nt = %lld differs from the %lld snapshot columns consumed",
+                       (long long)n_mu * Nt, (long long)m->pod_rows);
+    const size_t smem = sizeof(double) * ((size_t)Nt * n_mu + n_mu);
+    if (smem > 220 * 1024) return st_fail(ST_ERR_ARG, "st_rom_build_basis: Nt * n_mu too large for the temporal SVD");
+    st_internal_free_basis(m);
     ST_CUDA_TRY(cudaMalloc(&m->d_phi, sizeof(double) * N * ns));
     ST_CUDA_TRY(cudaMalloc(&m->d_T, sizeof(double) * (size_t)Nt * ns * nt));
-    ST_CUDA_TRY(cudaMemcpyAsync(m->d_phi, W, sizeof(double) * N * ns, cudaMemcpyDeviceToDevice, st));
+    ST_CUDA_TRY(cudaMemcpyAsync(m->d_phi, m->W.p, sizeof(double) * N * ns, cudaMemcpyDeviceToDevice, st));
     {
-        size_t smem = sizeof(double) * ((size_t)Nt * n_mu + n_mu);
-        if (smem > 220 * 1024) return st_fail(ST_ERR_ARG, "st_rom_build_basis: Nt * n_mu too large for the temporal SVD");
         if (smem > 48 * 1024)
             ST_CUDA_TRY(cudaFuncSetAttribute(temporal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         ST_PROF(m, "temporal_kernel");
-        temporal_kernel<<<ns, 512, smem, st>>>(Nt, n_mu, ns, nt, V, ldv, m->d_T, m->opt.jacobi_sweeps,
-                                               std::sqrt((double)Nt) * 2.220446049250313e-16, m->d_err);
+        temporal_kernel<<<ns, 512, smem, st>>>(Nt, n_mu, ns, nt, (const double*)m->V.p, m->pod_ldv, m->d_T,
+                                               m->opt.jacobi_sweeps, std::sqrt((double)Nt) * 2.220446049250313e-16,
+                                               m->d_err);
         ST_TRY(st_check_launch("temporal"));
     }
     m->ns = ns;
     m->nt = nt;
     m->Nt = Nt;
     return ST_OK;
+}
+
+}  // namespace
+
+extern "C" st_status st_pod_reset(st_model* m) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_pod_reset: NULL model");
+    pod_clear(m);
+    return ST_OK;
+}
+
+extern "C" st_status st_pod_update(st_model* m, int64_t n_cols, const double* snapshots, int32_t cols_per_update) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_pod_update: NULL model");
+    if (n_cols < 0 || (n_cols > 0 && !snapshots) || cols_per_update < 1)
+        return st_fail(ST_ERR_ARG, "st_pod_update: bad arguments");
+    if (n_cols == 0) return ST_OK;
+    return pod_update_impl(m, n_cols, snapshots, cols_per_update);
+}
+
+extern "C" st_status st_pod_finish(st_model* m, int32_t n_mu, int32_t Nt, int32_t ns, int32_t nt) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_pod_finish: NULL model");
+    if (n_mu < 1 || Nt < 1 || ns < 1 || nt < 1 || nt > Nt || nt > n_mu)
+        return st_fail(ST_ERR_ARG, "st_pod_finish: bad sizes");
+    return pod_finish_impl(m, n_mu, Nt, ns, nt);
+}
+
+extern "C" st_status st_pod_set_state(st_model* m, int32_t r, int64_t rows, const double* W, const double* sigma,
+                                      const double* V) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_pod_set_state: NULL model");
+    if (r < 0 || r > m->N || rows < 0 || (r > 0 && (!W || !sigma || (rows > 0 && !V))))
+        return st_fail(ST_ERR_ARG, "st_pod_set_state: bad arguments");
+    for (int i = 0; i < r; ++i)
+        if (!(sigma[i] >= 0.0) || !std::isfinite(sigma[i]) || (i > 0 && sigma[i] > sigma[i - 1]))
+            return st_fail(ST_ERR_ARG, "st_pod_set_state: sigma must be finite, non-negative and non-increasing");
+    pod_clear(m);
+    ST_TRY(pod_reserve(m, std::max(r, 1), std::max<int64_t>(rows, 1), std::max(r, 1)));
+    if (r > 0) {
+        ST_CUDA_TRY(cudaMemcpyAsync(m->W.p, W, sizeof(double) * m->N * r, cudaMemcpyDeviceToDevice, m->stream));
+        if (rows > 0)
+            ST_CUDA_TRY(cudaMemcpy2DAsync(m->V.p, sizeof(double) * m->pod_ldv, V, sizeof(double) * rows,
+                                          sizeof(double) * rows, r, cudaMemcpyDeviceToDevice, m->stream));
+        ST_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    }
+    m->pod_r = r;
+    m->pod_rows = rows;
+    m->sigma.assign(sigma, sigma + r);
+    st_oz_invalidate(m);
+    return ST_OK;
+}
+
+extern "C" st_status st_rom_build_basis(st_model* m, int32_t n_mu, int32_t Nt, const double* snapshots,
+                                        int32_t ns, int32_t nt, double* sigma_out, int32_t* rank_out) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_rom_build_basis: NULL model");
+    if (!snapshots || n_mu < 1 || Nt < 1 || ns < 1 || nt < 1)
+        return st_fail(ST_ERR_ARG, "st_rom_build_basis: bad arguments");
+    if (nt > Nt || nt > n_mu) return st_fail(ST_ERR_ARG, "st_rom_build_basis: nt > min(Nt, n_mu)");
+    if (n_mu > 64) return st_fail(ST_ERR_ARG, "st_rom_build_basis: at most 64 parameter samples");
+    // one update takes the snapshots of pod_block parameter samples, or
+    // pod_cols consecutive snapshot columns (1: the rank-one stream of
+    // Algorithm 2)
+    const int64_t ncols_all = (int64_t)n_mu * Nt;
+    const int pb = std::min<int>(m->opt.pod_block, n_mu);
+    const int bcols = m->opt.pod_cols > 0 ? (int)std::min<int64_t>(m->opt.pod_cols, ncols_all) : Nt * pb;
+    st_internal_free_basis(m);
+    pod_clear(m);
+    // V's rows for the whole snapshot set at once
+    ST_TRY(pod_reserve(m, 1, ncols_all, (int)std::min<int64_t>(m->opt.r_max, m->N)));
+    ST_TRY(pod_update_impl(m, ncols_all, snapshots, bcols));
+    const int r = m->pod_r;
+    if (rank_out) *rank_out = r;
+    if (sigma_out) for (int i = 0; i < r; ++i) sigma_out[i] = m->sigma[i];
+    return pod_finish_impl(m, n_mu, Nt, ns, nt);
 }

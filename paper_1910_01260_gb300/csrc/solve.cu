@@ -836,15 +836,16 @@ extern "C" st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double
     ST_TRY(scratch_address(m->device, &base));
     // scratch layout: [counter | npv (n_mu) | order (n_mu) | hist (nfull + 1)] then
     // one nfull x nfull FP64 workspace per resident block
+    // (one block's matrix in the factor precision: 4 bytes per entry in
+    // ST_FP32_LU, 8 otherwise)
     const size_t int_bytes = ((sizeof(int) * ((size_t)2 * n_mu + nfull + 1 + 16)) + 255) / 256 * 256;
-    const size_t mat_bytes = sizeof(double) * (size_t)nfull * nfull;
-    if (int_bytes + mat_bytes > kStaticScratchBytes)
+    const bool f32 = fp32_factors(m);
+    const size_t mat_t = (f32 ? sizeof(float) : sizeof(double)) * (size_t)nfull * nfull;
+    if (int_bytes + mat_t > kStaticScratchBytes)
         return st_fail(ST_ERR_ARG,
                        "st_rom_solve_static: n_mu = %d with ns*nt = %d needs %zu bytes of scratch, "
                        "more than the fixed %zu",
-                       n_mu, nfull, int_bytes + mat_bytes, kStaticScratchBytes);
-    const bool f32 = fp32_factors(m);
-    const size_t mat_t = (f32 ? sizeof(float) : sizeof(double)) * (size_t)nfull * nfull;
+                       n_mu, nfull, int_bytes + mat_t, kStaticScratchBytes);
     int nb = 0, cap_blocks = 0;
     size_t smem = 0;
     if (f32) ST_TRY(solve_plan<float>(m, 4, &nb, &smem, &cap_blocks));

@@ -65,3 +65,24 @@ def rel_max(a, b):
 
 def projector_dist(A, B):
     return float(np.abs(A @ A.T - B @ B.T).max())
+
+
+def _oracle_fom_one(args):
+    name, k, Nt = args
+    from workloads import problem_for
+    p = problem_for(name)
+    A = fom.affine_operator(p.rowptr, p.col, p.vals, p.theta(p.train_mu[k]))
+    return fom.fom_march(A, p.dt[:Nt], p.B, p.F[:Nt], None)
+
+
+def oracle_fom_train_parallel(name, Nt=None, procs=None):
+    """The oracle's snapshot blocks of every training parameter of a named
+    workload, one process per parameter (spawned, so safe after CUDA use)."""
+    import multiprocessing as mp
+    import os
+    from workloads import problem_for
+    p = problem_for(name)
+    Nt = p.Nt if Nt is None else Nt
+    procs = procs or min(len(p.train_mu), os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_oracle_fom_one, [(name, k, Nt) for k in range(len(p.train_mu))])

@@ -170,3 +170,52 @@ def test_pod_column_stream(pod_cols, r_max):
         U = np.concatenate(blocks, axis=1)
         assert np.abs(Wm @ np.diag(sig) @ Vm.T - U).max() < 1e-10 * sig[0]
     m.close()
+
+
+def test_reorthogonalisation_of_a_drifted_basis(monkeypatch):
+    """Algorithm 2's orthogonality check and QR re-orthogonalisation, made to
+    fire on the GPU: the state of one update with W drifted from orthogonality
+    (W0 (I + delta U), U strictly upper triangular) is installed, the next
+    block is folded in, and the result is compared with the oracle's update
+    of the same state."""
+    torch = __import__("torch")
+    p = problem_for("c1")
+    blocks = oracle_fom(p, p.train_mu[:2])
+    W0, s0, V0 = pod.incremental_update(None, None, None, blocks[0], 200, 1e-12, 1e-14)
+    r = W0.shape[1]
+    rng = np.random.default_rng(11)
+    Wd = W0 @ (np.eye(r) + 1e-7 * np.triu(rng.random((r, r)), 1))
+    fired = []
+    orig = pod.orthogonality_check
+
+    def recording(W, eps_svd):
+        out = orig(W, eps_svd)
+        fired.append(out[1])
+        return out
+
+    monkeypatch.setattr(pod, "orthogonality_check", recording)
+    W_o, s_o, V_o = pod.incremental_update(Wd, s0, V0, blocks[1], 200, 1e-12, 1e-14)
+    assert fired == [True]
+    m = make_model(p, r_max=200)
+    m.st_pod_set_state(r, p.Nt, dev_tensor(Wd.T.copy()), s0, dev_tensor(V0.T.copy()))
+    m.st_pod_update(p.Nt, _snap_tensor(blocks[1:2]), p.Nt)
+    sweeps, reorth = m.st_pod_get_stats()
+    assert reorth == 1
+    r2 = m.st_pod_get_dims()[0]
+    W = torch.zeros((r2, p.N), dtype=torch.float64, device="cuda:0")
+    V = torch.zeros((r2, 2 * p.Nt), dtype=torch.float64, device="cuda:0")
+    sig, _ = m.st_pod_get_state(W, V)
+    Wg, Vg = W.cpu().numpy().T, V.cpu().numpy().T
+    assert r2 == len(s_o)
+    k = min(40, r2)
+    assert np.abs(sig[:k] - s_o[:k]).max() < 1e-11 * s_o[0]
+    assert np.abs(Wg.T @ Wg - np.eye(r2)).max() < 1e-12
+    # the leading ns directions (well separated singular values): equal up to
+    # sign, since the QR keeps each column's orientation
+    lead = p.ns
+    assert np.abs(pod.canonical_signs(Wg[:, :lead]) - pod.canonical_signs(W_o[:, :lead])).max() < 1e-9
+    # the factorisation itself does not depend on signs
+    A_g = Wg @ np.diag(sig) @ Vg.T
+    A_o = W_o @ np.diag(s_o) @ V_o.T
+    assert np.abs(A_g - A_o).max() < 1e-11 * s_o[0]
+    m.close()

@@ -18,14 +18,14 @@ from workloads import make_problem
 pytestmark = pytest.mark.gpu
 
 
-def _model():
-    p = make_problem(dim=2, M=8, quad="s4", Nt=20, source="gaussian", g="ramp", ns=12, nt=5)
+def _model(ns=12, nt=5, **opts):
+    p = make_problem(dim=2, M=8, quad="s4", Nt=20, source="gaussian", g="ramp", ns=ns, nt=nt)
     rng = np.random.default_rng(9)
     Phi = np.linalg.qr(rng.standard_normal((p.N, p.ns)))[0]
     T = np.zeros((p.Nt, p.ns * p.nt))
     for i in range(p.ns):
         T[:, i::p.ns] = np.linalg.qr(rng.standard_normal((p.Nt, p.nt)))[0]
-    m = make_model(p)
+    m = make_model(p, **opts)
     m.st_model_set_basis(p.ns, p.nt, p.Nt, dev_tensor(Phi.T.copy()), dev_tensor(T.T.copy()))
     m.st_rom_assemble(p.dt, dev_B(p), p.F, None)
     return p, m
@@ -77,4 +77,33 @@ def test_static_solve_rejects_sizes_beyond_its_scratch():
         m.st_rom_solve_static(n, dummy, None, dummy)
     assert e.value.code == st.ST_ERR_ARG
     assert "32" in st.last_error() or "scratch" in st.last_error()
+    m.close()
+
+
+@pytest.mark.parametrize("precision,refine", [(0, 1), (2, 3)])  # FP64 LU; FP32 LU + 3 refinements
+def test_static_solve_at_n480_with_a_capped_grid(precision, refine):
+    """ns*nt = 480 (the largest size class of the benchmark): only ~17 FP64
+    (~34 FP32) factor matrices fit in the fixed scratch, fewer than the
+    allocating path's blocks, so the capped grid and the per-precision matrix
+    stride of the allocation-free path are the ones exercised."""
+    torch = __import__("torch")
+    p, m = _model(ns=40, nt=12, precision=precision, refine_steps=refine)
+    nf = p.ns * p.nt
+    rng = np.random.default_rng(31)
+    for call in range(2):
+        n = 200 + 40 * call
+        mu = p.mu_lo + rng.random((n, 2)) * (p.mu_hi - p.mu_lo)
+        choices = np.array([(40, 12), (30, 10), (20, 8), (10, 4)], dtype=np.int32)
+        sizes = choices[rng.integers(0, len(choices), n)]
+        sizes[:8] = (40, 12)
+        theta = p.theta(mu)
+        want, wres, wst = _run(m, m.st_rom_solve, theta, sizes, nf)
+        free0 = torch.cuda.mem_get_info()[0]
+        got, gres, gst = _run(m, m.st_rom_solve_static, theta, sizes, nf)
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert (wst == 0).all() and (gst == 0).all()
+        for k, (a, b) in enumerate(sizes):
+            assert rel_max(got[k, :a * b], want[k, :a * b]) < 1e-10
+        assert np.abs(gres - wres).max() < 1e-12
+    m.st_sync()
     m.close()
