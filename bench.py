@@ -85,6 +85,7 @@ def bench_config(args, world: int, Nt: int) -> dict:
             "parallelism": f"replicas{world}", "r_max": args.r_max,
             "online_precision": f"FP32 LU factors, FP64 residual + {ONLINE_REFINE} refinement steps",
             "eps_svd": EPS_SVD, "eps_sv": 1e-14, "pod_block": args.pod_block,
+            "fom_march": "cooperative grid march of the 16 parameters (st_options.fom_path auto)",
             "l2": "inputs larger than L2 (1.26 GB of snapshots written per step)"}
 
 
@@ -692,7 +693,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                 "all_solves_per_s": value,
                 "fp64_peak": {"tflops": fp64_peak, "probe_runs": fp64_probe,
                               "derived_tflops": FP64_DERIVED_TFLOPS,
-                              "how": "st_probe_fp64_fma: 4 blocks/SM x 256 threads x 8 FMA chains, "
+                              "how": "st_probe_fp64_fma: 4 blocks/SM x 256 threads x 16 FMA chains, "
                                      "CUDA events, best of 3"},
                 "kernels": kern,
                 "pod": pod_diag,
@@ -734,15 +735,38 @@ def run_case(case: str) -> None:
         snaps = torch.empty((n_train, Nt, prob.N), dtype=torch.float64, device=dev)
         m.st_fom_march(prob.theta(prob.train_mu), prob.dt[:Nt], None, B, prob.F[:Nt], snaps)
         if case == "fomfull":
-            iters = torch.zeros((Nt, n_train), dtype=torch.int32, device=dev)
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record(stream)
-            m.st_fom_march(prob.theta(prob.train_mu), prob.dt, None, B, prob.F, snaps, iters)
-            t1.record(stream)
-            m.st_sync()
-            print(json.dumps({"fom_ms": t0.elapsed_time(t1), "iters_mean": float(iters.float().mean()),
-                              "snap_checksum": float(snaps.abs().sum())}))
+            out = {}
+            ref = None
+            for name, path in (("grid", st.ST_FOM_GRID), ("cluster", st.ST_FOM_CLUSTER)):
+                m.st_model_set_options(fom_path=path)
+                iters = torch.zeros((Nt, n_train), dtype=torch.int32, device=dev)
+                m.st_fom_march(prob.theta(prob.train_mu), prob.dt, None, B, prob.F, snaps, iters)
+                m.st_sync()
+                ts = []
+                for _ in range(3):
+                    t0 = torch.cuda.Event(enable_timing=True)
+                    t1 = torch.cuda.Event(enable_timing=True)
+                    t0.record(stream)
+                    m.st_fom_march(prob.theta(prob.train_mu), prob.dt, None, B, prob.F, snaps, iters)
+                    t1.record(stream)
+                    m.st_sync()
+                    ts.append(t0.elapsed_time(t1))
+                if ref is None:
+                    ref = snaps.clone()
+                diff = float(((snaps - ref).abs().max() / ref.abs().max()).item())
+                out[name] = {"fom_ms": min(ts), "fom_ms_all": ts, "iters_mean": float(iters.float().mean()),
+                             "max_rel_diff_vs_grid": diff}
+            out["cluster_occupancy"] = m.st_fom_cluster_occupancy()
+            # cluster march of fewer samples (waves vs per-sample speed)
+            for nm in (1, 4, 8):
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(stream)
+                m.st_fom_march(prob.theta(prob.train_mu[:nm]), prob.dt, None, B, prob.F, snaps[:nm])
+                t1.record(stream)
+                m.st_sync()
+                out[f"cluster_{nm}mu_ms"] = t0.elapsed_time(t1)
+            print(json.dumps(out))
         if case == "podstream":
             out = {}
             for name, cols in (("blocks_of_8_samples", 0), ("rank_one_stream", 1)):

@@ -93,7 +93,18 @@ typedef struct {
     int32_t pod_cols;     /* when > 0: consecutive snapshot columns per update
                              instead of whole samples; 1 streams one snapshot
                              per update, the rank-one update of Algorithm 2  (0)      */
+    int32_t fom_path;     /* kernel of st_fom_march: ST_FOM_AUTO, ST_FOM_GRID or
+                             ST_FOM_CLUSTER                                 (AUTO)    */
 } st_options;
+
+/* Kernel of the full-order march (st_options.fom_path). */
+#define ST_FOM_AUTO     0  /* the faster kernel as measured on this library's
+                              workloads: the grid march                              */
+#define ST_FOM_GRID     1  /* one cooperative grid marching up to 32 samples in step  */
+#define ST_FOM_CLUSTER  2  /* one 8-CTA thread-block cluster per sample; needs one
+                              CTA's share of 4 vectors (4 * 8 * ceil(N/256) * 32
+                              bytes) to fit 200 KB of shared memory (N <= ~51,000),
+                              ST_ERR_ARG otherwise                                   */
 
 /* Fill *opt with the defaults shown above. */
 void st_options_default(st_options* opt);
@@ -109,9 +120,9 @@ const char* st_status_string(st_status s);
 int64_t st_kernel_launches(void);
 
 /* Measured FP64 fused multiply-add throughput of the current device
- * (synchronous): blocks_per_sm x (SM count) blocks of 256 threads each run 8
+ * (synchronous): blocks_per_sm x (SM count) blocks of 256 threads each run 16
  * independent FMA chains of `iters` steps, timed with CUDA events after one
- * shorter untimed launch.  *tflops = 2 * 8 * iters * threads / seconds / 1e12;
+ * shorter untimed launch.  *tflops = 2 * 16 * iters * threads / seconds / 1e12;
  * ms (may be NULL) receives the timed launch's milliseconds.  The roofline
  * denominator of the library's FP64-bound kernels.  ST_ERR_ARG for
  * blocks_per_sm outside [1, 32], iters < 1 or a NULL tflops. */
@@ -166,6 +177,14 @@ st_status st_sync(st_model* m);
 st_status st_fom_march(st_model* m, int32_t n_mu, const double* theta, int32_t Nt,
                        const double* dt, const double* u0, int32_t n_in, const double* B,
                        const double* F, double* snapshots, int32_t* iters, int32_t* status);
+
+/* Capacity of the cluster march on the current device for this model's
+ * operator: CTAs per cluster (one cluster per parameter sample), the number
+ * of such clusters the device runs at once (more samples run in waves), and
+ * the dynamic shared memory per CTA (0: the operator is too large for the
+ * cluster march).  Any pointer may be NULL. */
+st_status st_fom_cluster_occupancy(st_model* m, int32_t* cluster_ctas, int32_t* max_active_clusters,
+                                   int64_t* smem_bytes);
 
 /* Spatial and temporal bases by the incremental POD of Secs. 4.1-4.2
  * (synchronous).  The snapshot matrix U = [U_1 ... U_nmu] (N x Nt*n_mu,

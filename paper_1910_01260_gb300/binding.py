@@ -33,6 +33,9 @@ ST_FP32_ASSEMBLY = 1
 ST_FP32_LU = 2
 ST_DGEMM_SIMT = 0
 ST_DGEMM_OZAKI = 1
+ST_FOM_AUTO = 0
+ST_FOM_GRID = 1
+ST_FOM_CLUSTER = 2
 PROFILE_NAME_LEN = 64
 
 
@@ -46,7 +49,8 @@ class st_options(ctypes.Structure):
     _fields_ = [("tol", c_double), ("maxit", c_int32), ("eps_svd", c_double),
                 ("eps_sv", c_double), ("r_max", c_int32), ("precision", c_int32),
                 ("spin_limit", c_int64), ("refine_steps", c_int32), ("jacobi_sweeps", c_int32),
-                ("pod_block", c_int32), ("fp64_gemm", c_int32), ("pod_cols", c_int32)]
+                ("pod_block", c_int32), ("fp64_gemm", c_int32), ("pod_cols", c_int32),
+                ("fom_path", c_int32)]
 
 
 class st_model_info(ctypes.Structure):
@@ -91,6 +95,7 @@ _SIGS = {
     "st_model_load": (c_int32, [c_char_p, _P, POINTER(_P)]),
     "st_model_file_info": (c_int32, [c_char_p, POINTER(st_model_info)]),
     "st_probe_fp64_fma": (c_int32, [c_int32, c_int64, _P, _P]),
+    "st_fom_cluster_occupancy": (c_int32, [_P, _P, _P, _P]),
     "st_profile_enable": (c_int32, [_P, c_int32]),
     "st_profile_read": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_gemm_f64": (c_int32, [_P, c_int32, c_int32, c_int64, c_int64, c_int64, c_double, _P, c_int64, _P,
@@ -268,6 +273,14 @@ class Model:
         ro = np.zeros(1, dtype=np.int32)
         check(lib.st_pod_get_stats(self.handle, ptr(n), ptr(sw), int(n[0]), ptr(ro)))
         return sw[:n[0]].tolist(), int(ro[0])
+
+    def st_fom_cluster_occupancy(self):
+        """(CTAs per cluster, clusters resident at once, shared memory per CTA)."""
+        c = np.zeros(1, dtype=np.int32)
+        n = np.zeros(1, dtype=np.int32)
+        b = np.zeros(1, dtype=np.int64)
+        check(lib.st_fom_cluster_occupancy(self.handle, ptr(c), ptr(n), ptr(b)))
+        return int(c[0]), int(n[0]), int(b[0])
 
     def st_pod_reset(self) -> None:
         check(lib.st_pod_reset(self.handle))

@@ -13,7 +13,8 @@
 //   (64-bit) of the payload.  Sections, in this order, the first two always:
 //   "OPTS" f64 tol, i32 maxit, f64 eps_svd, f64 eps_sv, i32 r_max,
 //          i32 precision, i64 spin_limit, i32 refine_steps, i32 jacobi_sweeps,
-//          i32 pod_block, i32 fp64_gemm, i32 pod_cols   (packed, 64 bytes)
+//          i32 pod_block, i32 fp64_gemm, i32 pod_cols, i32 fom_path
+//          (packed, 68 bytes)
 //   "OPER" i64 N, i64 nnz, i32 Q, i32 0, i64 rowptr[N+1], i32 col[nnz]
 //          (padded to 8 bytes), f64 vals[Q][nnz]
 //   "PODS" i32 r, i32 n_updates, i64 rows, i32 n_reorth, i32 0, f64 sigma[r],
@@ -192,6 +193,7 @@ st_status parse(const std::vector<Section>& secs, Image& im, bool headers_only) 
         o.pod_block = in.get<int32_t>();
         o.fp64_gemm = in.get<int32_t>();
         o.pod_cols = in.get<int32_t>();
+        o.fom_path = in.get<int32_t>();
         if (!in.ok || in.at != in.n) return bad("OPTS");
     }
     auto skip = [&](In& in, uint64_t count, size_t size) {
@@ -368,6 +370,7 @@ extern "C" st_status st_model_save(st_model* m, const char* path) {
         o.put(p.pod_block);
         o.put(p.fp64_gemm);
         o.put(p.pod_cols);
+        o.put(p.fom_path);
         add("OPTS", o);
     }
     {

@@ -134,6 +134,7 @@ void st_options_default(st_options* o) {
     o->pod_block = 1;
     o->fp64_gemm = ST_DGEMM_OZAKI;
     o->pod_cols = 0;
+    o->fom_path = ST_FOM_AUTO;
 }
 
 const char* st_last_error(void) { return g_last_error.c_str(); }
@@ -161,6 +162,7 @@ static bool options_valid(const st_options& o) {
            o.spin_limit >= 1 && o.refine_steps >= 0 && o.refine_steps <= 16 && o.jacobi_sweeps >= 1 &&
            o.pod_block >= 1 && o.pod_block <= 64 && o.pod_cols >= 0 &&
            (o.fp64_gemm == ST_DGEMM_SIMT || o.fp64_gemm == ST_DGEMM_OZAKI) &&
+           (o.fom_path == ST_FOM_AUTO || o.fom_path == ST_FOM_GRID || o.fom_path == ST_FOM_CLUSTER) &&
            (o.precision == ST_FP64 || o.precision == ST_FP32_ASSEMBLY || o.precision == ST_FP32_LU);
 }
 

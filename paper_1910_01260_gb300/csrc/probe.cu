@@ -5,12 +5,13 @@
 
 namespace {
 
-constexpr int kChains = 8;  // independent FMA chains per thread (covers the pipe latency)
+constexpr int kChains = 16;  // independent FMA chains per thread (covers the pipe latency)
 
 __global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, double x, double y, double* sink) {
     double a[kChains];
 #pragma unroll
     for (int c = 0; c < kChains; ++c) a[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+#pragma unroll 4
     for (int64_t i = 0; i < iters; ++i) {
 #pragma unroll
         for (int c = 0; c < kChains; ++c) a[c] = fma(a[c], x, y);

@@ -15,10 +15,17 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-10
 
 
-def test_fom_c1_all_samples():
+@pytest.fixture(params=[1, 2], ids=["grid", "cluster"])
+def path(request):
+    """st_options.fom_path: the cooperative grid march (ST_FOM_GRID) and the
+    cluster-per-sample march (ST_FOM_CLUSTER)."""
+    return request.param
+
+
+def test_fom_c1_all_samples(path):
     p = problem_for("c1")
     mus = np.concatenate([p.train_mu, p.test_mu])       # 12 samples: padded group of 16
-    m = make_model(p)
+    m = make_model(p, fom_path=path)
     got, status, _ = gpu_fom(m, p, mus)
     assert (status == 0).all()
     ref = oracle_fom(p, mus)
@@ -28,11 +35,11 @@ def test_fom_c1_all_samples():
 
 
 @pytest.mark.parametrize("n_mu", [1, 2, 3, 33])
-def test_fom_group_shapes(n_mu):
+def test_fom_group_shapes(n_mu, path):
     # one sample (scalar path), padding inside a group, and two groups
     p = make_problem(dim=2, M=8, quad="s4", Nt=7, source="gaussian", g="ramp", u0="seeded")
     mus = p.mu_lo + np.random.default_rng(n_mu).random((n_mu, 2)) * (p.mu_hi - p.mu_lo)
-    m = make_model(p)
+    m = make_model(p, fom_path=path)
     got, status, _ = gpu_fom(m, p, mus, u0=p.u0)
     assert (status == 0).all()
     ref = oracle_fom(p, mus, u0=p.u0)
@@ -41,10 +48,10 @@ def test_fom_group_shapes(n_mu):
     m.close()
 
 
-def test_fom_c2_first_steps():
+def test_fom_c2_first_steps(path):
     p = problem_for("c2")
     mus = p.train_mu
-    m = make_model(p)
+    m = make_model(p, fom_path=path)
     got, status, it = gpu_fom(m, p, mus, Nt=12, with_iters=True)
     assert (status == 0).all()
     ref = oracle_fom(p, mus[:3], Nt=12)
@@ -59,11 +66,11 @@ def test_fom_c2_first_steps():
     m.close()
 
 
-def test_fom_pure_absorption_closed_form():
+def test_fom_pure_absorption_closed_form(path):
     p = make_problem(dim=1, M=16, quad="gl4", Nt=20, rho="homogeneous", source="none",
                      streaming=False, u0="seeded")
     mus = np.array([[0.5, 0.0], [1.3, 0.0]])
-    m = make_model(p)
+    m = make_model(p, fom_path=path)
     got, status, _ = gpu_fom(m, p, mus, u0=p.u0)
     assert (status == 0).all()
     for g, mu in zip(got, mus):
@@ -73,19 +80,19 @@ def test_fom_pure_absorption_closed_form():
     m.close()
 
 
-def test_fom_zero_input_gives_zero_state():
+def test_fom_zero_input_gives_zero_state(path):
     p = make_problem(dim=2, M=8, quad="s4", Nt=5, source="none")
-    m = make_model(p)
+    m = make_model(p, fom_path=path)
     got, status, _ = gpu_fom(m, p, p.train_mu)
     assert (status == 0).all()
     assert all(np.abs(g).max() == 0.0 for g in got)
     m.close()
 
 
-def test_fom_iteration_limit_reported():
+def test_fom_iteration_limit_reported(path):
     import paper_1910_01260_gb300 as st
     p = make_problem(dim=2, M=8, quad="s4", Nt=4, source="gaussian")
-    m = make_model(p, maxit=1)
+    m = make_model(p, maxit=1, fom_path=path)
     got, status, _ = gpu_fom(m, p, p.train_mu)
     assert (status == st.ST_ERR_NOT_CONVERGED).all()
     with pytest.raises(st.StError) as e:
@@ -95,11 +102,11 @@ def test_fom_iteration_limit_reported():
     m.close()
 
 
-def test_fom_nonfinite_sample_isolated():
+def test_fom_nonfinite_sample_isolated(path):
     import paper_1910_01260_gb300 as st
     p = make_problem(dim=2, M=8, quad="s4", Nt=4, source="gaussian")
     torch = __import__("torch")
-    m = make_model(p)
+    m = make_model(p, fom_path=path)
     theta = p.theta(p.train_mu)
     theta[1, 1] = np.nan
     snaps = torch.zeros((4, p.Nt, p.N), dtype=torch.float64, device="cuda:0")
@@ -117,16 +124,16 @@ def test_fom_nonfinite_sample_isolated():
     m.close()
 
 
-def test_fom_deterministic():
+def test_fom_deterministic(path):
     p = make_problem(dim=2, M=16, quad="s4", Nt=6, source="gaussian")
-    m = make_model(p)
+    m = make_model(p, fom_path=path)
     a, _, _ = gpu_fom(m, p, p.train_mu)
     b, _, _ = gpu_fom(m, p, p.train_mu)
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
     m.close()
 
 
-def test_fom_term_split_random_affine_operator():
+def test_fom_term_split_random_affine_operator(path):
     """A random 3-term affine operator whose entries have one, two or three
     nonzero terms (and some explicit all-zero entries): the march's
     term-split operator (shared single-term values scaled by theta_q, per
@@ -155,7 +162,7 @@ def test_fom_term_split_random_affine_operator():
     p = types.SimpleNamespace(N=N, rowptr=rowptr, col=cols.astype(np.int32), vals=vals, B=Bm, F=F, dt=dt,
                               Nt=Nt, theta=lambda t: np.asarray(t, dtype=np.float64))
     thetas = np.array([[1.0, 0.7, 0.3], [1.0, 1.3, 0.9], [0.5, 0.2, 1.1]])
-    m = make_model(p)
+    m = make_model(p, fom_path=path)
     got, status, _ = gpu_fom(m, p, thetas)
     assert (status == 0).all()
     for k, th in enumerate(thetas):
@@ -174,7 +181,7 @@ def test_fom_barrier_wait_runs_out_and_model_recovers():
     import paper_1910_01260_gb300 as st
     p = make_problem(dim=2, M=8, quad="s4", Nt=4, source="gaussian", g="ramp")
     mus = p.train_mu[:3]
-    m = make_model(p, spin_limit=1)
+    m = make_model(p, spin_limit=1, fom_path=1)   # grid barriers
     with pytest.raises(st.StError) as e:
         gpu_fom(m, p, mus)
         m.st_sync()
@@ -186,4 +193,37 @@ def test_fom_barrier_wait_runs_out_and_model_recovers():
     ref = oracle_fom(p, mus, Nt=4)
     for g, r in zip(got, ref):
         assert rel_max(g, r) < TOL
+    m.close()
+
+
+def test_fom_cluster_matches_grid_at_full_size():
+    """The two march kernels on the 2-D S4 operator of N = 49,152 (16
+    training parameters, 30 steps): same iteration counts within one and the
+    same snapshots to the march tolerance; the cluster march's first steps
+    against the oracle's sparse LU."""
+    p = problem_for("c4")
+    Nt = 30
+    out = {}
+    for path in (1, 2):
+        m = make_model(p, fom_path=path)
+        got, status, it = gpu_fom(m, p, p.train_mu, Nt=Nt, with_iters=True)
+        assert (status == 0).all()
+        out[path] = (got, it)
+        m.close()
+    for a, b in zip(out[1][0], out[2][0]):
+        assert rel_max(b, a) < TOL
+    assert np.abs(out[1][1] - out[2][1]).max() <= 1
+    ref = oracle_fom(p, p.train_mu[:2], Nt=Nt)
+    for g, r in zip(out[2][0][:2], ref):
+        assert rel_max(g, r) < TOL
+
+
+def test_fom_cluster_path_rejects_an_operator_too_large_for_it():
+    import paper_1910_01260_gb300 as st
+    # N = 72 x 72 cells x 12 directions = 62,208: one CTA's share of four vectors is 243 KB
+    p = make_problem(dim=2, M=72, quad="s4", Nt=2, source="gaussian")   # N = 62,208
+    m = make_model(p, fom_path=2)
+    with pytest.raises(st.StError) as e:
+        gpu_fom(m, p, p.train_mu[:1])
+    assert e.value.code == st.ST_ERR_ARG
     m.close()

@@ -206,8 +206,10 @@ def test_reorthogonalisation_of_a_drifted_basis(monkeypatch):
     V = torch.zeros((r2, 2 * p.Nt), dtype=torch.float64, device="cuda:0")
     sig, _ = m.st_pod_get_state(W, V)
     Wg, Vg = W.cpu().numpy().T, V.cpu().numpy().T
-    assert r2 == len(s_o)
-    k = min(40, r2)
+    # directions at the eps_sv cut (sigma ~ 1e-14 sigma_1) are kept or dropped
+    # by rounding: the ranks may differ by one or two
+    assert abs(r2 - len(s_o)) <= 2
+    k = min(40, r2, len(s_o))
     assert np.abs(sig[:k] - s_o[:k]).max() < 1e-11 * s_o[0]
     assert np.abs(Wg.T @ Wg - np.eye(r2)).max() < 1e-12
     # the leading ns directions (well separated singular values): equal up to
@@ -216,6 +218,6 @@ def test_reorthogonalisation_of_a_drifted_basis(monkeypatch):
     assert np.abs(pod.canonical_signs(Wg[:, :lead]) - pod.canonical_signs(W_o[:, :lead])).max() < 1e-9
     # the factorisation itself does not depend on signs
     A_g = Wg @ np.diag(sig) @ Vg.T
-    A_o = W_o @ np.diag(s_o) @ V_o.T
+    A_o = W_o @ np.diag(s_o) @ V_o.T   # a direction at the cut adds ~1e-14 sigma_1
     assert np.abs(A_g - A_o).max() < 1e-11 * s_o[0]
     m.close()

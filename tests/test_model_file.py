@@ -40,8 +40,8 @@ def model_bytes(N=6, Q=2, r=3, rows=8, ns=2, nt=2, Nt=4, reduced=True, surrogate
     nnz = int(rowptr[-1])
     col = np.array([[i, (i + 1) % N] for i in range(N)], dtype=np.int32).ravel()
     vals = rng.standard_normal((Q, nnz))
-    opts = struct.pack("<diddiiqiiiii", 1e-13, 1000, 1e-12, 1e-14, 256, 0, 20000000, 1, 40, 1, 1, 0)
-    assert len(opts) == 64
+    opts = struct.pack("<diddiiqiiiiii", 1e-13, 1000, 1e-12, 1e-14, 256, 0, 20000000, 1, 40, 1, 1, 0, 0)
+    assert len(opts) == 68
     secs = [section(b"OPTS", opts),
             section(b"OPER", pad8(struct.pack("<qqii", N, nnz, Q, 0) + rowptr.tobytes() + col.tobytes())
                     + vals.tobytes())]
@@ -107,7 +107,7 @@ def test_damaged_files_are_rejected(st, tmp_path, damage):
         b[16 + 8:16 + 16] = struct.pack("<Q", 60)  # OPTS claims 60 bytes
     elif damage == "section_order":
         # swap the OPTS and OPER section tags (checksums cover payloads only)
-        off2 = 16 + 16 + 64 + 8
+        off2 = 16 + 16 + 68 + 8
         b[16:20], b[off2:off2 + 4] = b"OPER", b"OPTS"
     elif damage == "unknown_section":
         b[12:16] = struct.pack("<I", 7)
