@@ -423,6 +423,16 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     for _ in range(args.warmup):
         step(False)
     m.st_sync()
+    # launch plan of the batched solve: the cached tuned plan for this device,
+    # basis, precision and size mix, or a tuning run on this batch (untimed)
+    from paper_1910_01260_gb300 import tuning
+    plan_key = tuning.plan_key(torch.cuda.get_device_name(dev), ns, nt, st.ST_FP32_LU, ONLINE_REFINE,
+                               N_BATCH, sizes)
+    tune_scratch = torch.zeros_like(uhat)
+    solve_plan = tuning.load_or_tune(m, plan_key, st.ST_FP32_LU, N_BATCH, th_d, sz_d, tune_scratch, reps=2)
+    solve_plan["key"] = plan_key
+    del tune_scratch
+    m.st_sync()
     barrier()
     phase_ms = {k: [] for k in ("fom", "pod", "assemble", "solve", "reconstruct")}
     t_start = torch.cuda.Event(enable_timing=True)
@@ -508,6 +518,25 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                         "max_rel_res": float(res.max()), "status_ok": int((s_status == 0).sum()),
                         "max_rel_diff_vs_fp64": diff}
     m.st_model_set_options(precision=st.ST_FP32_LU, refine_steps=ONLINE_REFINE)
+    # the tuned plan against the library's default plan, in this run
+    plan_ms = {}
+    tuned = m.st_rom_solve_get_plan(st.ST_FP32_LU)
+    for name, pl in (("default", None), ("tuned", solve_plan["plan"])):
+        m.st_rom_solve_set_plan(st.ST_FP32_LU, pl)
+        m.st_rom_solve(N_BATCH, th_d, sz_d, uhat, res, s_status)
+        torch.cuda.synchronize()
+        o0 = torch.cuda.Event(enable_timing=True)
+        o1 = torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for _ in range(args.steps):
+            m.st_rom_solve(N_BATCH, th_d, sz_d, uhat, res, s_status)
+        o1.record(stream)
+        torch.cuda.synchronize()
+        plan_ms[name] = o0.elapsed_time(o1) / args.steps
+    solve_plan.update({"resolved": tuned, "default_ms_this_run": plan_ms["default"],
+                       "tuned_ms_this_run": plan_ms["tuned"],
+                       "speedup_this_run": plan_ms["default"] / plan_ms["tuned"]})
+    solve_plan.pop("candidates", None)
     uhat.copy_(step_uhat)
     m.st_sync()
 
@@ -677,6 +706,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                 "phases_ms": phases,
                 "online_solves_per_s": N_BATCH / ((phases["solve"] + phases["reconstruct"]) / 1e3),
                 "online_modes": online,
+                "solve_plan": solve_plan,
                 "spatial_rom": spatial,
                 "residual_certificate": certificate,
                 "surrogate": surrogate,

@@ -400,6 +400,53 @@ st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double* theta,
                               const int32_t* ns_nt, double* uhat, double* rel_res,
                               int32_t* status);
 
+/* Launch plan of the batched solve (st_rom_solve, st_rom_solve_static and the
+ * surrogate's fallback), one per factor precision (ST_FP32_LU, or the FP64
+ * factors of ST_FP64 / ST_FP32_ASSEMBLY).  No counterpart in the paper: these
+ * are tile and scheduling choices of this library's kernel.
+ *   panel        LU panel width: 4, 8, 16 or 32 (0 = the widest that fits
+ *                shared memory, at most 32)
+ *   ctas_per_sm  resident CTAs per SM, capped by occupancy (0 = the default:
+ *                4 with FP32 factors, 2 with FP64 factors)
+ *   order        queue order of the samples (ST_ORDER_*)
+ * Plans with the same panel width give the same results bit for bit (a
+ * sample is solved by one CTA in a fixed order whichever CTA takes it); the
+ * panel width sets the blocking of the LU and so its rounding (results agree
+ * to the solve's accuracy). */
+typedef struct {
+    int32_t panel;
+    int32_t ctas_per_sm;
+    int32_t order;
+} st_solve_plan;
+#define ST_ORDER_LARGEST_FIRST  0  /* largest ns_p * nt_p first (default)  */
+#define ST_ORDER_SMALLEST_FIRST 1  /* smallest first                       */
+#define ST_ORDER_INPUT          2  /* the samples' own order, no size sort  */
+
+/* Install a plan for `precision`'s factor arithmetic; NULL restores the
+ * defaults.  ST_ERR_ARG for invalid fields.  Host-only bookkeeping. */
+st_status st_rom_solve_set_plan(st_model* m, int32_t precision, const st_solve_plan* plan);
+
+/* The plan the solve would use now for `precision`, with the defaults and
+ * limits resolved (panel width after shrinking to fit, CTAs per SM after the
+ * occupancy cap).  Requires the reduced operators (ST_ERR_STATE otherwise). */
+st_status st_rom_solve_get_plan(st_model* m, int32_t precision, st_solve_plan* plan);
+
+/* Autotuner (synchronous): times st_rom_solve on the caller's batch (theta,
+ * ns_nt, uhat as for st_rom_solve; uhat is overwritten) under the model's
+ * current precision for every candidate plan -- the default plan first, then
+ * each panel width in {8, 16, 32} that fits shared memory x each CTAs-per-SM
+ * count from 1 to min(occupancy, 4) x each queue order -- one untimed run and
+ * `reps` runs timed with CUDA events on the model's stream each (best kept),
+ * then installs the fastest for that precision.  Optional outputs: the first
+ * `cap` candidates and their best times in cands/ms, the number of
+ * candidates in *n_cands, the best time in *best_ms, the default plan's time
+ * in *default_ms; *best receives the installed plan (fields 0 where the
+ * default is kept).  ST_ERR_STATE before assembly, ST_ERR_ARG for bad
+ * arguments; a failing solve aborts the tuning and keeps the previous plan. */
+st_status st_rom_solve_tune(st_model* m, int32_t n_mu, const double* theta, const int32_t* ns_nt,
+                            double* uhat, int32_t reps, int32_t cap, st_solve_plan* cands, float* ms,
+                            int32_t* n_cands, st_solve_plan* best, float* best_ms, float* default_ms);
+
 /* Reconstruction u^st ~= Phi_st uhat (Eq. ststateapproximation) by blocks:
  *   C[i,k] = sum_j uhat[i + ns_p j] phi_t^{i,j}[k],  u^k = Phi_s C[:,k].
  *   uhat  dev [n_mu x ns*nt] as written by st_rom_solve; ns_nt as there

@@ -36,6 +36,9 @@ ST_DGEMM_OZAKI = 1
 ST_FOM_AUTO = 0
 ST_FOM_GRID = 1
 ST_FOM_CLUSTER = 2
+ST_ORDER_LARGEST_FIRST = 0
+ST_ORDER_SMALLEST_FIRST = 1
+ST_ORDER_INPUT = 2
 PROFILE_NAME_LEN = 64
 
 
@@ -57,6 +60,10 @@ class st_model_info(ctypes.Structure):
     _fields_ = [("version", c_int32), ("n_terms", c_int32), ("n_rows", c_int64), ("nnz", c_int64),
                 ("pod_rows", c_int64), ("pod_rank", c_int32), ("ns", c_int32), ("nt", c_int32),
                 ("Nt", c_int32), ("assembled", c_int32), ("surrogate", c_int32), ("n_params", c_int64)]
+
+
+class st_solve_plan(ctypes.Structure):
+    _fields_ = [("panel", c_int32), ("ctas_per_sm", c_int32), ("order", c_int32)]
 
 
 class st_affine_csr(ctypes.Structure):
@@ -96,6 +103,10 @@ _SIGS = {
     "st_model_file_info": (c_int32, [c_char_p, POINTER(st_model_info)]),
     "st_probe_fp64_fma": (c_int32, [c_int32, c_int64, _P, _P]),
     "st_fom_cluster_occupancy": (c_int32, [_P, _P, _P, _P]),
+    "st_rom_solve_set_plan": (c_int32, [_P, c_int32, POINTER(st_solve_plan)]),
+    "st_rom_solve_get_plan": (c_int32, [_P, c_int32, POINTER(st_solve_plan)]),
+    "st_rom_solve_tune": (c_int32, [_P, c_int32, _P, _P, _P, c_int32, c_int32, _P, _P, _P,
+                                    POINTER(st_solve_plan), _P, _P]),
     "st_profile_enable": (c_int32, [_P, c_int32]),
     "st_profile_read": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P]),
     "st_gemm_f64": (c_int32, [_P, c_int32, c_int32, c_int64, c_int64, c_int64, c_double, _P, c_int64, _P,
@@ -354,6 +365,36 @@ class Model:
     def st_rom_solve_static(self, n_mu, theta, ns_nt, uhat, rel_res=None, status=None) -> None:
         check(lib.st_rom_solve_static(self.handle, n_mu, ptr(theta), ptr(ns_nt), ptr(uhat),
                                       ptr(rel_res), ptr(status)))
+
+    def st_rom_solve_set_plan(self, precision, plan=None) -> None:
+        """plan: dict(panel, ctas_per_sm, order) or None for the defaults."""
+        if plan is None:
+            check(lib.st_rom_solve_set_plan(self.handle, int(precision), None))
+            return
+        p = st_solve_plan(int(plan["panel"]), int(plan["ctas_per_sm"]), int(plan["order"]))
+        check(lib.st_rom_solve_set_plan(self.handle, int(precision), ctypes.byref(p)))
+
+    def st_rom_solve_get_plan(self, precision) -> dict:
+        p = st_solve_plan()
+        check(lib.st_rom_solve_get_plan(self.handle, int(precision), ctypes.byref(p)))
+        return {"panel": p.panel, "ctas_per_sm": p.ctas_per_sm, "order": p.order}
+
+    def st_rom_solve_tune(self, n_mu, theta, ns_nt, uhat, reps=2, cap=64) -> dict:
+        """Time every candidate plan on this batch and install the fastest."""
+        cands = (st_solve_plan * cap)()
+        ms = np.zeros(cap, dtype=np.float32)
+        n = np.zeros(1, dtype=np.int32)
+        best = st_solve_plan()
+        bms = np.zeros(1, dtype=np.float32)
+        dms = np.zeros(1, dtype=np.float32)
+        check(lib.st_rom_solve_tune(self.handle, n_mu, ptr(theta), ptr(ns_nt), ptr(uhat), int(reps), cap,
+                                    ctypes.addressof(cands), ptr(ms), ptr(n), ctypes.byref(best), ptr(bms),
+                                    ptr(dms)))
+        k = min(int(n[0]), cap)
+        return {"best": {"panel": best.panel, "ctas_per_sm": best.ctas_per_sm, "order": best.order},
+                "best_ms": float(bms[0]), "default_ms": float(dms[0]), "n_candidates": int(n[0]),
+                "candidates": [{"panel": cands[i].panel, "ctas_per_sm": cands[i].ctas_per_sm,
+                                "order": cands[i].order, "ms": float(ms[i])} for i in range(k)]}
 
     def st_rom_reconstruct(self, n_mu, uhat, ns_nt, u=None, n_out=0, Cout=None, y=None) -> None:
         check(lib.st_rom_reconstruct(self.handle, n_mu, ptr(uhat), ptr(ns_nt), ptr(u), n_out,

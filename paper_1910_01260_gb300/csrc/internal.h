@@ -119,6 +119,13 @@ struct st_model {
     DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_oz, ws_solve, ws_misc, ws_srom;
     OzSlot oz_slot[kOzSlots];
 
+    // launch plan of the batched reduced solve per factor precision ([0] FP64
+    // factors, [1] FP32 factors): panel width, CTAs per SM, queue order (0 =
+    // library default), set by st_rom_solve_set_plan or st_rom_solve_tune
+    struct SolvePlanCfg {
+        int nb = 0, per_sm = 0, order = 0;
+    } solve_cfg[2];
+
     // learned surrogate mu -> uhat (3-layer MLP, FP32 masters, BF16 copies)
     struct Mlp {
         int n_in = 2, hidden = 256, n_out = 0;

@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
     for (;;) {
         if (tid == 0) {
             const unsigned int it = atomicAdd(g.queue, 1u);
-            s_item = it < (unsigned)g.n_mu ? g.order[it] : -1;
+            s_item = it < (unsigned)g.n_mu ? (g.order ? g.order[it] : (int)it) : -1;
         }
         __syncthreads();
         const int p = s_item;
@@ -629,10 +629,13 @@ __global__ void size_hist_kernel(int n_mu, int ns, int nt, const int32_t* __rest
     }
 }
 
-__global__ void size_scan_kernel(int nfull, int* hist) {
+// Exclusive scan of the size histogram: largest size first (descending) or
+// smallest first (ascending).
+__global__ void size_scan_kernel(int nfull, int* hist, int ascending) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         int run = 0;
-        for (int s = nfull; s >= 0; --s) {
+        for (int i = 0; i <= nfull; ++i) {
+            const int s = ascending ? i : nfull - i;
             const int c = hist[s];
             hist[s] = run;
             run += c;
@@ -659,12 +662,16 @@ bool fp32_factors(const st_model* m) { return m->opt.precision == ST_FP32_LU; }
 
 // Shared-memory plan and grid for solve_kernel<T>; the panel width shrinks if
 // a wide model does not fit.
+// The plan's panel width (if set) and CTAs-per-SM cap replace the defaults
+// (panel 32, cap_per_sm).
 template <typename T>
 st_status solve_plan(st_model* m, int cap_per_sm, int* nb_out, size_t* smem_out, int* blocks_out) {
     const int ns = m->ns, nfull = ns * m->nt;
     if (nfull > kRowsPerThread * NT)
         return st_fail(ST_ERR_ARG, "st_rom_solve: ns*nt = %d above %d", nfull, kRowsPerThread * NT);
-    int nb = 32;
+    const st_model::SolvePlanCfg& cfg = m->solve_cfg[sizeof(T) == sizeof(float) ? 1 : 0];
+    int nb = cfg.nb > 0 ? cfg.nb : 32;
+    if (cfg.per_sm > 0) cap_per_sm = cfg.per_sm;
     int max_optin = 0;
     ST_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
     while (nb > 4 && solve_smem(nfull, ns, nb, sizeof(T)) > (size_t)max_optin) nb /= 2;
@@ -733,17 +740,19 @@ extern "C" st_status st_rom_solve(st_model* m, int32_t n_mu, const double* theta
     int* npv = (int*)((char*)m->ws_solve.p + ws_bytes);
     int* order = npv + n_mu;
     int* hist = order + n_mu;
-    ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
-    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n_mu + 255) / 256, 4 * m->num_sms));
-    {
+    const int order_mode = m->solve_cfg[f32 ? 1 : 0].order;
+    if (order_mode != ST_ORDER_INPUT) {
+        ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
+        const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n_mu + 255) / 256, 4 * m->num_sms));
         ST_PROF(m, "size_sort_kernels");
         size_hist_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, ns_nt, npv, hist);
-        size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
+        size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist, order_mode == ST_ORDER_SMALLEST_FIRST);
         size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
         ST_TRY(st_check_launch("solve order"));
     }
     ST_CUDA_TRY(cudaMemsetAsync(m->d_bar + 3, 0, sizeof(unsigned int), st));
-    SolveArgs g = solve_args(m, n_mu, theta, ns_nt, uhat, rel_res, status, order, m->d_bar + 3, ws, nb);
+    SolveArgs g = solve_args(m, n_mu, theta, ns_nt, uhat, rel_res, status,
+                             order_mode == ST_ORDER_INPUT ? nullptr : order, m->d_bar + 3, ws, nb);
     ST_PROF(m, f32 ? "solve_kernel<float>" : "solve_kernel<double>");
     if (f32) solve_kernel<float><<<blocks, NT, smem, st>>>(g);
     else solve_kernel<double><<<blocks, NT, smem, st>>>(g);
@@ -859,19 +868,156 @@ extern "C" st_status st_rom_solve_static(st_model* m, int32_t n_mu, const double
     int* hist = order + n_mu;
     double* ws = reinterpret_cast<double*>(sb + int_bytes);
     // the array keeps the previous call's contents: zero what must start at zero
-    ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
     ST_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st));
-    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n_mu + 255) / 256, 4 * m->num_sms));
-    {
+    const int order_mode = m->solve_cfg[f32 ? 1 : 0].order;
+    if (order_mode != ST_ORDER_INPUT) {
+        ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * (nfull + 1), st));
+        const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n_mu + 255) / 256, 4 * m->num_sms));
         ST_PROF(m, "size_sort_kernels");
         size_hist_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, ns_nt, npv, hist);
-        size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist);
+        size_scan_kernel<<<1, 32, 0, st>>>(nfull, hist, order_mode == ST_ORDER_SMALLEST_FIRST);
         size_scatter_kernel<<<gb, 256, 0, st>>>(n_mu, npv, hist, order);
         ST_TRY(st_check_launch("solve_static order"));
     }
-    SolveArgs g = solve_args(m, n_mu, theta, ns_nt, uhat, rel_res, status, order, queue, ws, nb);
+    SolveArgs g = solve_args(m, n_mu, theta, ns_nt, uhat, rel_res, status,
+                             order_mode == ST_ORDER_INPUT ? nullptr : order, queue, ws, nb);
     ST_PROF(m, f32 ? "solve_kernel<float>" : "solve_kernel<double>");
     if (f32) solve_kernel<float><<<blocks, NT, smem, st>>>(g);
     else solve_kernel<double><<<blocks, NT, smem, st>>>(g);
     return st_check_launch("solve_static");
+}
+
+// ---------------------------------------------------------------------------
+// Launch plans of the batched solve and their tuner.
+namespace {
+
+int plan_index(int32_t precision) { return precision == ST_FP32_LU ? 1 : 0; }
+
+bool plan_valid(const st_solve_plan& p) {
+    return (p.panel == 0 || p.panel == 4 || p.panel == 8 || p.panel == 16 || p.panel == 32) && p.ctas_per_sm >= 0 &&
+           p.ctas_per_sm <= 8 && (p.order == ST_ORDER_LARGEST_FIRST || p.order == ST_ORDER_SMALLEST_FIRST ||
+                                  p.order == ST_ORDER_INPUT);
+}
+
+// The plan solve_plan<T> resolves for the model's current configuration.
+template <typename T>
+st_status resolved_plan(st_model* m, int default_cap, st_solve_plan* out) {
+    int nb = 0, blocks = 0;
+    size_t smem = 0;
+    ST_TRY(solve_plan<T>(m, default_cap, &nb, &smem, &blocks));
+    out->panel = nb;
+    out->ctas_per_sm = blocks / std::max(m->num_sms, 1);
+    out->order = m->solve_cfg[sizeof(T) == sizeof(float) ? 1 : 0].order;
+    return ST_OK;
+}
+
+}  // namespace
+
+extern "C" st_status st_rom_solve_set_plan(st_model* m, int32_t precision, const st_solve_plan* plan) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_rom_solve_set_plan: NULL model");
+    if (precision != ST_FP64 && precision != ST_FP32_ASSEMBLY && precision != ST_FP32_LU)
+        return st_fail(ST_ERR_ARG, "st_rom_solve_set_plan: unknown precision %d", precision);
+    st_model::SolvePlanCfg c;
+    if (plan) {
+        if (!plan_valid(*plan))
+            return st_fail(ST_ERR_ARG, "st_rom_solve_set_plan: panel must be 0, 4, 8, 16 or 32, ctas_per_sm in "
+                                       "[0, 8], order an ST_ORDER_* value");
+        c.nb = plan->panel;
+        c.per_sm = plan->ctas_per_sm;
+        c.order = plan->order;
+    }
+    m->solve_cfg[plan_index(precision)] = c;
+    return ST_OK;
+}
+
+extern "C" st_status st_rom_solve_get_plan(st_model* m, int32_t precision, st_solve_plan* plan) {
+    if (!m || !plan) return st_fail(ST_ERR_ARG, "st_rom_solve_get_plan: NULL argument");
+    if (!m->assembled) return st_fail(ST_ERR_STATE, "st_rom_solve_get_plan: reduced operators not assembled");
+    if (precision == ST_FP32_LU) return resolved_plan<float>(m, 4, plan);
+    return resolved_plan<double>(m, 2, plan);
+}
+
+extern "C" st_status st_rom_solve_tune(st_model* m, int32_t n_mu, const double* theta, const int32_t* ns_nt,
+                                       double* uhat, int32_t reps, int32_t cap, st_solve_plan* cands, float* ms,
+                                       int32_t* n_cands, st_solve_plan* best, float* best_ms, float* default_ms) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_rom_solve_tune: NULL model");
+    if (!m->assembled) return st_fail(ST_ERR_STATE, "st_rom_solve_tune: reduced operators not assembled");
+    if (n_mu < 1 || !theta || !uhat || reps < 1 || cap < 0 || !best)
+        return st_fail(ST_ERR_ARG, "st_rom_solve_tune: bad arguments");
+    const bool f32 = fp32_factors(m);
+    const int idx = f32 ? 1 : 0;
+    const int ns = m->ns, nfull = ns * m->nt;
+    const size_t tsize = f32 ? sizeof(float) : sizeof(double);
+    const st_model::SolvePlanCfg saved = m->solve_cfg[idx];
+    int max_optin = 0;
+    ST_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
+    // candidates: every panel width that fits, every CTAs-per-SM count the
+    // occupancy allows (up to 4), every queue order; the default plan first
+    std::vector<st_model::SolvePlanCfg> list;
+    list.push_back(st_model::SolvePlanCfg{});
+    for (int nb : {8, 16, 32}) {
+        const size_t smem = solve_smem(nfull, ns, nb, tsize);
+        if (smem > (size_t)max_optin) continue;
+        int occ = 0;
+        const void* fn = f32 ? (const void*)solve_kernel<float> : (const void*)solve_kernel<double>;
+        ST_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, smem));
+        for (int c = 1; c <= std::min(occ, 4); ++c)
+            for (int o : {ST_ORDER_LARGEST_FIRST, ST_ORDER_SMALLEST_FIRST, ST_ORDER_INPUT})
+                list.push_back(st_model::SolvePlanCfg{nb, c, o});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ST_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return st_fail(ST_ERR_CUDA, "st_rom_solve_tune: event creation failed");
+    }
+    st_status rc = ST_OK;
+    float best_t = 0.0f, def_t = 0.0f;
+    st_model::SolvePlanCfg best_c{};
+    int written = 0;
+    for (size_t i = 0; i < list.size() && rc == ST_OK; ++i) {
+        m->solve_cfg[idx] = list[i];
+        rc = st_rom_solve(m, n_mu, theta, ns_nt, uhat, nullptr, nullptr);  // warm (workspace growth)
+        float tmin = 0.0f;
+        for (int r = 0; r < reps && rc == ST_OK; ++r) {
+            cudaEventRecord(e0, m->stream);
+            rc = st_rom_solve(m, n_mu, theta, ns_nt, uhat, nullptr, nullptr);
+            cudaEventRecord(e1, m->stream);
+            if (rc != ST_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = st_fail(ST_ERR_CUDA, "st_rom_solve_tune: event wait failed");
+                break;
+            }
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            tmin = r == 0 ? t : std::min(tmin, t);
+        }
+        if (rc != ST_OK) break;
+        if (i == 0) def_t = tmin;
+        if (i == 0 || tmin < best_t) {
+            best_t = tmin;
+            best_c = list[i];
+        }
+        if (cands && ms && written < cap) {
+            st_solve_plan pl{list[i].nb, list[i].per_sm, list[i].order};
+            cands[written] = pl;
+            ms[written] = tmin;
+            ++written;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ST_OK) {
+        m->solve_cfg[idx] = saved;
+        return rc;
+    }
+    m->solve_cfg[idx] = best_c;
+    if (n_cands) *n_cands = (int32_t)list.size();
+    best->panel = best_c.nb;
+    best->ctas_per_sm = best_c.per_sm;
+    best->order = best_c.order;
+    if (best_ms) *best_ms = best_t;
+    if (default_ms) *default_ms = def_t;
+    return ST_OK;
 }
