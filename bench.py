@@ -738,6 +738,125 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     m.close()
 
 
+def run_c3(n_train: int, group: int, pod_block: int, n_solve: int) -> None:
+    """Config c3 at full size: 2-D S6 transport on 256 x 256 cells (N =
+    1,572,864), Nt = 500, n_train training parameters (the 8 x 4 grid), basis
+    (40, 12) with r_max = 512.  The snapshot set (201 GB in FP64 for 32
+    parameters) is never resident: parameter groups are marched into one
+    reused buffer and each group is folded into the incremental SVD
+    (st_pod_update) before the next group is marched.  Then the temporal
+    bases, the assembly, a batch of reduced solves at (40, 12), and the ROM's
+    error against the FOM on two test parameters.  Prints one JSON line."""
+    import torch
+
+    import paper_1910_01260_gb300 as st
+    from workloads import c4_batch, problem_for
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    fp64_peak = max(st.st_probe_fp64_fma()[0] for _ in range(2))
+    prob = problem_for("c3")
+    N, Nt, ns = prob.N, prob.Nt, prob.ns
+    nt = min(prob.nt, n_train)  # the temporal rank is at most the sample count
+    train = prob.train_mu[:n_train]
+    m = st.Model(prob.rowptr, prob.col, prob.vals, st.options(r_max=512, eps_svd=EPS_SVD, pod_block=pod_block),
+                 stream=stream.cuda_stream)
+    free0 = torch.cuda.mem_get_info()[0]
+    B = torch.tensor(prob.B.T.copy(), device=dev)
+    snaps = torch.empty((group, Nt, N), dtype=torch.float64, device=dev)
+    iters = torch.zeros((Nt, group), dtype=torch.int32, device=dev)
+    status = torch.zeros(group, dtype=torch.int32, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    t_fom = t_pod = 0.0
+    it_total = 0
+    ok = True
+    m.st_profile_enable(True)
+    m.st_pod_reset()
+    min_free = free0
+    for g0 in range(0, n_train, group):
+        g = min(group, n_train - g0)
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        m.st_fom_march(prob.theta(train[g0:g0 + g]), prob.dt, None, B, prob.F, snaps[:g], iters[:, :g],
+                       status[:g])
+        e1.record(stream)
+        m.st_pod_update(g * Nt, snaps[:g], pod_block * Nt)
+        e2.record(stream)
+        m.st_sync()
+        t_fom += e0.elapsed_time(e1)
+        t_pod += e1.elapsed_time(e2)
+        it_total += int(iters[:, :g].sum())
+        ok = ok and int(status[:g].abs().max()) == 0
+        min_free = min(min_free, torch.cuda.mem_get_info()[0])
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    m.st_pod_finish(n_train, Nt, ns, nt)
+    e1.record(stream)
+    m.st_sync()
+    t_temporal = e0.elapsed_time(e1)
+    sig, rank = m.st_pod_get_state()
+    sweeps, reorth = m.st_pod_get_stats()
+    W = torch.zeros((rank, N), dtype=torch.float64, device=dev)
+    m.st_pod_get_state(W)
+    orth = float((W @ W.T - torch.eye(rank, dtype=torch.float64, device=dev)).abs().max())
+    del W
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    m.st_rom_assemble(prob.dt, B, prob.F, None)
+    e1.record(stream)
+    m.st_sync()
+    t_asm = e0.elapsed_time(e1)
+    prof = m.st_profile_read()
+    m.st_profile_enable(False)
+    # online: a batch at the full (40, 12), FP32 LU factors + 3 FP64 refinements
+    m.st_model_set_options(precision=st.ST_FP32_LU, refine_steps=ONLINE_REFINE)
+    mu_b, _ = c4_batch(n_solve, prob)
+    th_b = torch.tensor(prob.theta(mu_b), device=dev)
+    uh = torch.zeros((n_solve, ns * nt), dtype=torch.float64, device=dev)
+    rr = torch.zeros(n_solve, dtype=torch.float64, device=dev)
+    sst = torch.zeros(n_solve, dtype=torch.int32, device=dev)
+    m.st_rom_solve(n_solve, th_b, None, uh, rr, sst)
+    m.st_sync()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    m.st_rom_solve(n_solve, th_b, None, uh, rr, sst)
+    e1.record(stream)
+    m.st_sync()
+    t_solve = e0.elapsed_time(e1)
+    # ROM error against the FOM on two test parameters (full fields)
+    test = prob.test_mu[:2]
+    th_t = prob.theta(test)
+    fsn = snaps[:2]
+    m.st_fom_march(th_t, prob.dt, None, B, prob.F, fsn)
+    ut = torch.zeros((2, ns * nt), dtype=torch.float64, device=dev)
+    m.st_rom_solve(2, torch.tensor(th_t, device=dev), None, ut)
+    ur = torch.zeros((2, Nt, N), dtype=torch.float64, device=dev)
+    m.st_rom_reconstruct(2, ut, None, ur)
+    m.st_sync()
+    errs = [float(torch.linalg.norm(fsn[j] - ur[j]) / torch.linalg.norm(fsn[j])) for j in range(2)]
+    # FOM roofline: per BiCGSTAB iteration and parameter 4 nnz + 26 N flops,
+    # per step and parameter 2 nnz + 8 N (the residual of the initial iterate)
+    fom_flops = it_total * (4.0 * prob.nnz + 26.0 * N) + Nt * n_train * (2.0 * prob.nnz + 8.0 * N)
+    fom_tf = fom_flops / (t_fom * 1e-3) / 1e12
+    out = {"case": "c3", "workload": (f"c3: 2-D S6 transport 256x256 (N={N}), Nt={Nt}, {n_train} training mu in "
+                                      f"groups of {group}, basis (40,12), r_max 512, {n_solve} online solves"),
+           "fom_ms": t_fom, "fom_mu_per_s": n_train / (t_fom / 1e3), "fom_status_ok": ok,
+           "fom_bicgstab_iters_mean": it_total / (n_train * Nt),
+           "fom_roofline": {"bound": "alu", "achieved": fom_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                            "frac": fom_tf / fp64_peak, "peak_source": "of measured: FP64 FMA probe"},
+           "pod_ms": t_pod, "pod_updates": len(sweeps), "pod_block": pod_block, "temporal_ms": t_temporal,
+           "rank": rank, "reorthogonalisations": reorth, "W_orthonormality": orth,
+           "sigma_rel": {str(i): float(sig[i] / sig[0]) for i in (1, 10, 40, 100, 200, 400) if i < len(sig)},
+           "assemble_ms": t_asm, "solve_ms": t_solve, "solves_per_s": n_solve / (t_solve / 1e3),
+           "solve_status_ok": int((sst == 0).sum()), "solve_max_rel_res": float(rr.max()),
+           "rom_rel_err_vs_fom_test": errs,
+           "device_bytes_used_max": int(torch.cuda.mem_get_info()[1] - min_free),
+           "snapshot_buffer_bytes": int(snaps.numel() * 8),
+           "kernels_offline": {k: [round(v[0], 2), v[1]] for k, v in list(prof.items())[:14]}}
+    print(json.dumps(out), flush=True)
+    m.close()
+
+
 def run_case(case: str) -> None:
     """One small workload of a single kernel family, for profiling with ncu.
     fom: FOM march of the 16 training parameters, 10 steps (one launch);
@@ -897,8 +1016,15 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=200)
     ap.add_argument("--case", default=None, help="run one profiling workload: fom, fomfull, pod, podstream, solve, spatial, "
-                         "residual, mlp")
+                         "residual, mlp; or c3 (the full-size 2-D S6 configuration, streamed by parameter group)")
+    ap.add_argument("--c3-mu", type=int, default=32, help="c3: training parameters")
+    ap.add_argument("--c3-group", type=int, default=4, help="c3: parameters marched per snapshot group")
+    ap.add_argument("--c3-pod-block", type=int, default=1, help="c3: samples per incremental-SVD update")
+    ap.add_argument("--c3-solves", type=int, default=4096, help="c3: online solves at (40, 12)")
     args = ap.parse_args()
+    if args.case == "c3":
+        run_c3(args.c3_mu, args.c3_group, args.c3_pod_block, args.c3_solves)
+        return
     if args.case:
         run_case(args.case)
         return
