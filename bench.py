@@ -857,6 +857,77 @@ def run_c3(n_train: int, group: int, pod_block: int, n_solve: int) -> None:
     m.close()
 
 
+def run_certificate(tol: float, max_iter: int) -> None:
+    """The complete a posteriori certificate of Theorem 3 on the batched
+    online workload (2-D S4, N = 49,152, Nt = 200, (40, 12) basis built from
+    the 16 training parameters): for one parameter of each (ns, nt) class,
+    sqrt(Nt) ||(A^st)^-1||_2 max_k ||r^k|| from the library (power-iteration
+    constant, residual norms of the ROM trajectory) against the true error
+    max_k ||u^k - u~^k|| from a FOM march.  Prints one JSON line."""
+    import torch
+
+    import paper_1910_01260_gb300 as st
+    from workloads import c4_batch, problem_for
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    prob = problem_for("c4")
+    N, Nt, ns, nt = prob.N, prob.Nt, prob.ns, prob.nt
+    m = st.Model(prob.rowptr, prob.col, prob.vals, st.options(eps_svd=EPS_SVD, pod_block=POD_BLOCK),
+                 stream=stream.cuda_stream)
+    B = torch.tensor(prob.B.T.copy(), device=dev)
+    n_train = len(prob.train_mu)
+    snaps = torch.empty((n_train, Nt, N), dtype=torch.float64, device=dev)
+    m.st_fom_march(prob.theta(prob.train_mu), prob.dt, None, B, prob.F, snaps)
+    m.st_rom_build_basis(n_train, Nt, snaps, ns, nt)
+    m.st_rom_assemble(prob.dt, B, prob.F, None)
+    del snaps
+    mu_b, sizes = c4_batch(N_BATCH, prob)
+    pick = [int(np.where((sizes[:, 0] == a) & (sizes[:, 1] == b))[0][0])
+            for a, b in sorted({tuple(x) for x in sizes.tolist()})]
+    th = prob.theta(mu_b[pick])
+    sz = torch.tensor(sizes[pick], device=dev)
+    n = len(pick)
+    uh = torch.zeros((n, ns * nt), dtype=torch.float64, device=dev)
+    m.st_rom_solve(n, torch.tensor(th, device=dev), sz, uh)
+    U = torch.zeros((n, Nt, N), dtype=torch.float64, device=dev)
+    m.st_rom_reconstruct(n, uh, sz, U)
+    rn = torch.zeros((n, Nt), dtype=torch.float64, device=dev)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    m.st_rom_residual_norms(th, prob.dt, None, B, prob.F, U, rn)
+    e1.record(stream)
+    m.st_sync()
+    t0 = time.perf_counter()
+    try:
+        const, iters = m.st_fom_st_inverse_norm(th, prob.dt, max_iter=max_iter, tol=tol)
+        converged = True
+    except st.StError as err:
+        if err.code != st.ST_ERR_NOT_CONVERGED:
+            raise
+        const, iters, converged = None, max_iter, False
+    t_const = time.perf_counter() - t0
+    fsn = torch.empty((n, Nt, N), dtype=torch.float64, device=dev)
+    e2.record(stream)
+    m.st_fom_march(th, prob.dt, None, B, prob.F, fsn)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e3.record(stream)
+    m.st_sync()
+    out = {"case": "certificate", "tol": tol, "power_iterations": iters, "converged": converged,
+           "constant_s": t_const, "residual_ms": e0.elapsed_time(e1), "fom_ms": e2.elapsed_time(e3), "classes": {}}
+    R = rn.cpu().numpy()
+    for j, k in enumerate(pick):
+        err = float((fsn[j] - U[j]).norm(dim=1).max())
+        cl = {"true_max_err": err, "max_residual": float(R[j].max()),
+              "rel_true_err": err / float(fsn[j].norm(dim=1).max())}
+        if const is not None:
+            cl["inverse_norm"] = float(const[j])
+            cl["bound"] = float(np.sqrt(Nt) * const[j] * R[j].max())
+            cl["bound_over_err"] = cl["bound"] / err
+        out["classes"][f"({sizes[k][0]},{sizes[k][1]})"] = cl
+    print(json.dumps(out), flush=True)
+    m.close()
+
+
 def run_case(case: str) -> None:
     """One small workload of a single kernel family, for profiling with ncu.
     fom: FOM march of the 16 training parameters, 10 steps (one launch);
@@ -1016,12 +1087,18 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=200)
     ap.add_argument("--case", default=None, help="run one profiling workload: fom, fomfull, pod, podstream, solve, spatial, "
-                         "residual, mlp; or c3 (the full-size 2-D S6 configuration, streamed by parameter group)")
+                         "residual, mlp; c3 (the full-size 2-D S6 configuration, streamed by parameter group); "
+                         "certificate (Theorem 3's bound with the library's constant)")
+    ap.add_argument("--cert-tol", type=float, default=1e-4, help="certificate: power-iteration tolerance")
+    ap.add_argument("--cert-iters", type=int, default=300, help="certificate: power-iteration cap")
     ap.add_argument("--c3-mu", type=int, default=32, help="c3: training parameters")
     ap.add_argument("--c3-group", type=int, default=4, help="c3: parameters marched per snapshot group")
     ap.add_argument("--c3-pod-block", type=int, default=1, help="c3: samples per incremental-SVD update")
     ap.add_argument("--c3-solves", type=int, default=4096, help="c3: online solves at (40, 12)")
     args = ap.parse_args()
+    if args.case == "certificate":
+        run_certificate(args.cert_tol, args.cert_iters)
+        return
     if args.case == "c3":
         run_c3(args.c3_mu, args.c3_group, args.c3_pod_block, args.c3_solves)
         return

@@ -506,6 +506,27 @@ st_status st_rom_residual_norms(st_model* m, int32_t n_mu, const double* theta, 
                                 const double* B, const double* F, const double* U,
                                 double* rnorm);
 
+/* Stability constant of the space-time error bound (Theorem 3),
+ *   ||u^st - u~^st||_2 <= ||(A^st)^{-1}||_2 ||r^st||_2,
+ * for n_mu parameter samples (1..32): A^st is the block lower bidiagonal
+ * matrix of the backward-Euler march (diagonal blocks I - dt_k A(mu), sub-
+ * diagonal blocks -I; Eqs. st-fom, stsystemmat).  Estimated by power iteration
+ * on (A^st)^{-T} (A^st)^{-1} from a seeded start vector: each iteration is one
+ * full-order march with a per-step source (applying (A^st)^{-1}) and one march
+ * of the transposed terms A_q^T over the reversed steps (applying
+ * (A^st)^{-T}); the transposed terms are built on the first call from the
+ * model's copy of the operator and kept.  The estimate sqrt(||w||) (w the
+ * power iterate before normalisation) rises monotonically to the norm from
+ * below; iteration stops once every sample's estimate changed by at most
+ * tol (relative) in one iteration.  Synchronous.
+ *   theta host [n_mu x Q]; dt host [Nt] (> 0); seed of the start vector
+ *   norm  host [n_mu]: the estimates; iters_used host or NULL
+ * A march that fails is reported with its status; ST_ERR_NOT_CONVERGED when
+ * max_iter iterations did not reach tol (norm still holds the estimates).
+ * Workspace: 3 n_mu Nt N doubles. */
+st_status st_fom_st_inverse_norm(st_model* m, int32_t n_mu, const double* theta, int32_t Nt, const double* dt,
+                                 int32_t max_iter, double tol, uint64_t seed, double* norm, int32_t* iters_used);
+
 /* Learned surrogate mu -> uhat (no counterpart in the paper; it serves the
  * many-query use the paper motivates): a 3-layer MLP 2 -> 256 -> 256 -> ns*nt
  * with exact-erf GELU, FP32 master weights, BF16 copies on the tensor cores,

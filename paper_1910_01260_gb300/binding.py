@@ -103,6 +103,7 @@ _SIGS = {
     "st_model_file_info": (c_int32, [c_char_p, POINTER(st_model_info)]),
     "st_probe_fp64_fma": (c_int32, [c_int32, c_int64, _P, _P]),
     "st_fom_cluster_occupancy": (c_int32, [_P, _P, _P, _P]),
+    "st_fom_st_inverse_norm": (c_int32, [_P, c_int32, _P, c_int32, _P, c_int32, c_double, ctypes.c_uint64, _P, _P]),
     "st_rom_solve_set_plan": (c_int32, [_P, c_int32, POINTER(st_solve_plan)]),
     "st_rom_solve_get_plan": (c_int32, [_P, c_int32, POINTER(st_solve_plan)]),
     "st_rom_solve_tune": (c_int32, [_P, c_int32, _P, _P, _P, c_int32, c_int32, _P, _P, _P,
@@ -292,6 +293,19 @@ class Model:
         b = np.zeros(1, dtype=np.int64)
         check(lib.st_fom_cluster_occupancy(self.handle, ptr(c), ptr(n), ptr(b)))
         return int(c[0]), int(n[0]), int(b[0])
+
+    def st_fom_st_inverse_norm(self, theta, dt, max_iter=200, tol=1e-8, seed=7):
+        """(||(A^st)^-1||_2 estimates per sample, iterations used)."""
+        th = _host(theta, np.float64)
+        if th.ndim == 1:
+            th = th[None]
+        dth = _host(dt, np.float64)
+        out = np.zeros(th.shape[0], dtype=np.float64)
+        it = np.zeros(1, dtype=np.int32)
+        self._keep = [th, dth]
+        check(lib.st_fom_st_inverse_norm(self.handle, th.shape[0], ptr(th), dth.shape[0], ptr(dth), int(max_iter),
+                                         float(tol), ctypes.c_uint64(seed), ptr(out), ptr(it)))
+        return out, int(it[0])
 
     def st_pod_reset(self) -> None:
         check(lib.st_pod_reset(self.handle))

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 SOURCES = ["model.cu", "dgemm.cu", "fom.cu", "pod.cu", "assemble.cu", "solve.cu",
-           "reconstruct.cu", "tc_host.cu", "mlp.cu", "ozaki.cu", "srom.cu", "residual.cu", "io.cu", "probe.cu"]
+           "reconstruct.cu", "tc_host.cu", "mlp.cu", "ozaki.cu", "srom.cu", "residual.cu", "io.cu", "probe.cu", "certificate.cu"]
 
 
 def _nvcc() -> str:

@@ -64,6 +64,7 @@ struct FomArgs {
     int n_in;
     const double* B;  // [N x n_in]
     const double* F;  // [Nt x n_in]
+    const double* src;  // [n_mu x Nt x N] extra right-hand side z_k per step, or NULL
     double *x, *r, *rh, *p, *v, *s, *t;  // [N * LD]
     double* hist;                        // [kHist x N * LD] solutions of the last kHist levels
     double* partial;                     // [2 x grid * NSLOT * LD]
@@ -202,7 +203,9 @@ __device__ __forceinline__ void grid_reduce(const double* partial, double (*s_re
     __syncthreads();
 }
 
-template <int LD>
+// SRC: the right-hand side of step k also carries a per-sample vector z_k
+// (a general source, as in the space-time system A^st u = z).
+template <int LD, bool SRC>
 __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(FomArgs a) {
     using C = Cfg<LD>;
     constexpr int VEC = C::VEC, LPR = C::LPR, RPB = C::RPB, NW = C::NW;
@@ -297,7 +300,10 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
 #pragma unroll
                 for (int u = 0; u < VEC; ++u) {
                     const bool on = s_state[p0 + u] != S_FAILED && s_state[p0 + u] != S_PAD;
-                    const double b = fma(h, bf, ukv[u]);
+                    double b = fma(h, bf, ukv[u]);
+                    if constexpr (SRC) {
+                        if (p0 + u < a.n_mu) b += __ldg(a.src + ((int64_t)(p0 + u) * a.Nt + k) * N + row);
+                    }
                     rr[u] = on ? fma(h, Au[u], b - xv[u]) : 0.0;
                     zero[u] = 0.0;
                     if (on) {
@@ -1123,11 +1129,13 @@ st_status run_cluster(st_model* m, int n_mu, const double* d_theta, int Nt, cons
 
 template <int LD>
 st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const double* d_dt,
-                    const double* u0, int n_in, const double* B, const double* d_F, double* snap,
-                    int32_t* iters, int32_t* status, int32_t* d_iters_tmp) {
+                    const double* u0, int n_in, const double* B, const double* d_F, const double* src,
+                    double* snap, int32_t* iters, int32_t* status, int32_t* d_iters_tmp) {
     const int64_t N = m->N, ell = m->ell_size, mx = m->mx_size;
     const size_t vec = (size_t)N * LD;
-    int blocks = st_coop_blocks(m, fom_march_kernel<LD>, NT, 0, ST_FOM_BLOCKS_PER_SM);
+    const void* kern = src ? (const void*)fom_march_kernel<LD, true> : (const void*)fom_march_kernel<LD, false>;
+    int blocks = st_coop_blocks(m, fom_march_kernel<LD, false>, NT, 0, ST_FOM_BLOCKS_PER_SM);
+    if (src) blocks = std::min(blocks, st_coop_blocks(m, fom_march_kernel<LD, true>, NT, 0, ST_FOM_BLOCKS_PER_SM));
     if (blocks < 1) return st_fail(ST_ERR_CUDA, "fom: cooperative occupancy query failed");
     const int64_t rpb = Cfg<LD>::RPB;
     const int64_t nchunks = (N + rpb - 1) / rpb;
@@ -1163,6 +1171,7 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     a.n_in = n_in;
     a.B = B;
     a.F = d_F;
+    a.src = src;
     a.x = vecs;
     a.r = vecs + vec;
     a.rh = vecs + 2 * vec;
@@ -1181,18 +1190,18 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     a.bar = GridBarrier{m->d_bar, m->d_bar + 1, m->d_bar + 2, m->d_err, m->opt.spin_limit};
     void* args[] = {&a};
     ST_PROF(m, "fom_march_kernel");
-    ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)fom_march_kernel<LD>, dim3(blocks), dim3(NT),
-                                            args, 0, m->stream));
+    ST_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, 0, m->stream));
         st_count_launch();
     return ST_OK;
 }
 
 }  // namespace
 
-extern "C" st_status st_fom_march(st_model* m, int32_t n_mu, const double* theta, int32_t Nt,
-                                  const double* dt, const double* u0, int32_t n_in,
-                                  const double* B, const double* F, double* snapshots,
-                                  int32_t* iters, int32_t* status) {
+// The march of st_fom_march with an optional per-step source src (dev
+// [n_mu x Nt x N], added to the right-hand side of every step; grid march).
+st_status st_internal_fom_march(st_model* m, int32_t n_mu, const double* theta, int32_t Nt, const double* dt,
+                                const double* u0, int32_t n_in, const double* B, const double* F,
+                                const double* src, double* snapshots, int32_t* iters, int32_t* status) {
     if (!m) return st_fail(ST_ERR_ARG, "st_fom_march: NULL model");
     if (n_mu < 1 || Nt < 1 || n_in < 0) return st_fail(ST_ERR_ARG, "st_fom_march: bad sizes");
     if (!theta || !dt || !snapshots) return st_fail(ST_ERR_ARG, "st_fom_march: NULL argument");
@@ -1215,8 +1224,8 @@ extern "C" st_status st_fom_march(st_model* m, int32_t n_mu, const double* theta
     // the 2-D S4 operator of N = 49,152 with 16 samples: 95 ms grid, 167 ms
     // cluster -- 15 clusters of 8 CTAs are resident at once, so 16 samples
     // take two waves, and one sample on 8 SMs takes 85 ms)
-    const bool use_cluster = m->opt.fom_path == ST_FOM_CLUSTER && cluster_smem(m) > 0;
-    if (m->opt.fom_path == ST_FOM_CLUSTER && !use_cluster)
+    const bool use_cluster = !src && m->opt.fom_path == ST_FOM_CLUSTER && cluster_smem(m) > 0;
+    if (!src && m->opt.fom_path == ST_FOM_CLUSTER && !use_cluster)
         return st_fail(ST_ERR_ARG, "st_fom_march: the cluster march does not fit N = %lld", (long long)m->N);
     if (use_cluster) {
         // samples in groups of at most 64 clusters (the iteration counts are
@@ -1240,14 +1249,15 @@ extern "C" st_status st_fom_march(st_model* m, int32_t n_mu, const double* theta
         double* snap = snapshots + (size_t)g0 * Nt * m->N;
         int32_t* st = status ? status + g0 : nullptr;
         const double* th = d_theta + (size_t)g0 * Q;
+        const double* sg = src ? src + (size_t)g0 * Nt * m->N : nullptr;
         st_status rc;
         switch (ld) {
-            case 1: rc = run_group<1>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, snap, iters, st, d_it); break;
-            case 2: rc = run_group<2>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, snap, iters, st, d_it); break;
-            case 4: rc = run_group<4>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, snap, iters, st, d_it); break;
-            case 8: rc = run_group<8>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, snap, iters, st, d_it); break;
-            case 16: rc = run_group<16>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, snap, iters, st, d_it); break;
-            default: rc = run_group<32>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, snap, iters, st, d_it); break;
+            case 1: rc = run_group<1>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 2: rc = run_group<2>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 4: rc = run_group<4>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 8: rc = run_group<8>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 16: rc = run_group<16>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            default: rc = run_group<32>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
         }
         if (rc != ST_OK) return rc;
         if (iters) {
@@ -1258,6 +1268,13 @@ extern "C" st_status st_fom_march(st_model* m, int32_t n_mu, const double* theta
         }
     }
     return ST_OK;
+}
+
+extern "C" st_status st_fom_march(st_model* m, int32_t n_mu, const double* theta, int32_t Nt,
+                                  const double* dt, const double* u0, int32_t n_in,
+                                  const double* B, const double* F, double* snapshots,
+                                  int32_t* iters, int32_t* status) {
+    return st_internal_fom_march(m, n_mu, theta, Nt, dt, u0, n_in, B, F, nullptr, snapshots, iters, status);
 }
 
 extern "C" st_status st_fom_cluster_occupancy(st_model* m, int32_t* cluster_ctas, int32_t* max_active_clusters,

@@ -116,7 +116,10 @@ struct st_model {
     unsigned int* d_bar = nullptr;  // [4]: arrival count, generation, abort flag, queue head
 
     // scratch buffers (grown on demand, reused across calls)
-    DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_oz, ws_solve, ws_misc, ws_srom;
+    DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_oz, ws_solve, ws_misc, ws_srom, ws_cert;
+    // the transposed terms A_q^T (built on first use by the Theorem 3
+    // stability-constant estimate)
+    st_model* adj = nullptr;
     OzSlot oz_slot[kOzSlots];
 
     // launch plan of the batched reduced solve per factor precision ([0] FP64
@@ -233,3 +236,9 @@ st_status st_internal_install_reduced(st_model* m, const double* Ahat, const dou
 st_status st_internal_mlp_install(st_model* m, int hidden, const float* params, const float* adam_m,
                                   const float* adam_v, const double* mean, const double* stdv, const double* lo,
                                   const double* hi, int64_t adam_t);
+
+// The full-order march of st_fom_march with an optional per-step source
+// src (dev [n_mu x Nt x N]) added to the right-hand side of step k.
+st_status st_internal_fom_march(st_model* m, int32_t n_mu, const double* theta, int32_t Nt, const double* dt,
+                                const double* u0, int32_t n_in, const double* B, const double* F,
+                                const double* src, double* snapshots, int32_t* iters, int32_t* status);
