@@ -560,6 +560,38 @@ st_status st_rom_surrogate_infer(st_model* m, int32_t n, const double* mu, const
                                  double gate, double* uhat, double* rel_res, int32_t* used_fallback,
                                  int32_t* n_fallback);
 
+/* Reference preconditioner for the reduced space-time systems (no counterpart
+ * in the paper): Ahat^st at n_ref reference parameters (e.g. the training
+ * grid) is assembled and inverted in FP32 (Gauss-Jordan with partial
+ * pivoting, one CTA per reference) and kept by the model.  Requires the
+ * reduced operators; replaced by the next call.
+ *   mu_ref host [n_ref x 2] (the parameters, for nearest-reference lookup),
+ *   theta_ref host [n_ref x Q]; 1 <= n_ref <= 1024, ns*nt <= 4096.
+ * Synchronous; ST_ERR_SINGULAR if a reference matrix has a zero pivot. */
+st_status st_rom_precond_build(st_model* m, int32_t n_ref, const double* mu_ref, const double* theta_ref);
+
+/* Reduced solves by preconditioned Richardson refinement, started from the
+ * surrogate's prediction (ST_GUESS_SURROGATE) or from zero (ST_GUESS_ZERO):
+ *   x <- x + P_g (fhat^st - Ahat^st(mu) x),  P_g = Ahat^st(mu_g)^{-1},
+ * with mu_g the reference nearest to mu (coordinates scaled by the
+ * references' spread).  Every step evaluates the residual of the whole batch
+ * through the affine pieces of Ahat^st (FP32 products combined in FP64, as
+ * the surrogate's gate) and stops as soon as every sample satisfies
+ * ||rhs - Ahat^st x|| / ||rhs|| <= gate, or after max_iter corrections;
+ * samples still above the gate are then solved by the batched LU of
+ * st_rom_solve (their rel_res is the LU's).  Full (ns, nt) only.  The
+ * residual's FP32 products limit the reachable gate to about 1e-6.
+ *   mu dev [n x 2], theta dev [n x Q], uhat dev [n x ns*nt] (output),
+ *   rel_res dev [n], used_fallback dev [n]; iters_run host or NULL:
+ *   corrections applied; n_fallback host or NULL.
+ * Requires st_rom_precond_build (ST_ERR_STATE otherwise) and, with
+ * ST_GUESS_SURROGATE, a trained surrogate.  Synchronous. */
+#define ST_GUESS_SURROGATE 0
+#define ST_GUESS_ZERO      1
+st_status st_rom_refine(st_model* m, int32_t n, const double* mu, const double* theta, int32_t guess, double gate,
+                        int32_t max_iter, double* uhat, double* rel_res, int32_t* used_fallback,
+                        int32_t* iters_run, int32_t* n_fallback);
+
 /* Current FP32 surrogate parameters (host [count], layout as for init);
  * params may be NULL to query count.  Synchronous. */
 st_status st_rom_surrogate_params(st_model* m, float* params, int64_t* count);

@@ -39,6 +39,8 @@ ST_FOM_CLUSTER = 2
 ST_ORDER_LARGEST_FIRST = 0
 ST_ORDER_SMALLEST_FIRST = 1
 ST_ORDER_INPUT = 2
+ST_GUESS_SURROGATE = 0
+ST_GUESS_ZERO = 1
 PROFILE_NAME_LEN = 64
 
 
@@ -123,6 +125,8 @@ _SIGS = {
                                          ctypes.c_uint64, _P]),
     "st_rom_surrogate_infer": (c_int32, [_P, c_int32, _P, _P, c_double, _P, _P, _P, _P]),
     "st_rom_surrogate_params": (c_int32, [_P, _P, _P]),
+    "st_rom_precond_build": (c_int32, [_P, c_int32, _P, _P]),
+    "st_rom_refine": (c_int32, [_P, c_int32, _P, _P, c_int32, c_double, c_int32, _P, _P, _P, _P, _P]),
     "st_rom_surrogate_loss_grad": (c_int32, [_P, c_int32, _P, _P, _P, _P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -464,8 +468,21 @@ def _surrogate_methods():
                                              ptr(grad), ptr(loss)))
         return float(loss[0]), grad
 
+    def st_rom_precond_build(self, mu_ref, theta_ref):
+        mr = _host(mu_ref, np.float64)
+        tr = _host(theta_ref, np.float64)
+        check(lib.st_rom_precond_build(self.handle, mr.shape[0], ptr(mr), ptr(tr)))
+
+    def st_rom_refine(self, n, mu, theta, guess, gate, max_iter, uhat, rel_res, used_fallback):
+        """(corrections applied, fallback count)."""
+        it = np.zeros(1, dtype=np.int32)
+        nf = np.zeros(1, dtype=np.int32)
+        check(lib.st_rom_refine(self.handle, n, ptr(mu), ptr(theta), int(guess), float(gate), int(max_iter),
+                                ptr(uhat), ptr(rel_res), ptr(used_fallback), ptr(it), ptr(nf)))
+        return int(it[0]), int(nf[0])
+
     for f in (st_rom_surrogate_train, st_rom_surrogate_infer, st_rom_surrogate_params,
-              st_rom_surrogate_loss_grad):
+              st_rom_surrogate_loss_grad, st_rom_precond_build, st_rom_refine):
         setattr(Model, f.__name__, f)
 
 

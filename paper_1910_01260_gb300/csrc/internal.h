@@ -117,6 +117,14 @@ struct st_model {
 
     // scratch buffers (grown on demand, reused across calls)
     DevBuf ws_fom, ws_pod, ws_pod2, ws_gemm, ws_oz, ws_solve, ws_misc, ws_srom, ws_cert;
+    // reference preconditioner of the reduced space-time systems: FP32
+    // inverses of Ahat^st at n_ref reference parameters (n x n each, row
+    // major) and those parameters
+    struct Precond {
+        int n_ref = 0, n = 0;
+        std::vector<double> mu;  // [n_ref x 2]
+        DevBuf inv, work;
+    } prec;
     // the transposed terms A_q^T (built on first use by the Theorem 3
     // stability-constant estimate)
     st_model* adj = nullptr;

@@ -706,3 +706,438 @@ st_status st_internal_mlp_install(st_model* m, int hidden, const float* params, 
     s.trained = true;
     return ST_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Preconditioned refinement of the reduced space-time solves.
+//
+// Ahat^st(mu) is affine in theta(mu), and the systems at nearby parameters
+// are close: with P_g = Ahat^st(mu_g)^{-1} at the reference parameter mu_g
+// nearest to mu, the Richardson iteration
+//     x <- x + P_g (fhat^st - Ahat^st(mu) x)
+// contracts fast (||I - P_g Ahat^st(mu)|| small).  Each step is two batched
+// products over the batch: the residual through the affine pieces K_q of
+// Ahat^st (the gate's operator) and the correction through P_g, with the
+// samples sorted by reference so that every 64-row tile of the correction
+// product uses one P_g.  The start is the surrogate's prediction (or zero),
+// so the network's accuracy buys iterations; answers still above the gate
+// after the iterations fall back to the batched LU.
+namespace {
+
+constexpr int kTile = 64;  // rows per tile of the batched products
+
+// [A | I] of Ahat^st(theta_g) in FP32 (row major, ld 2n), one reference per
+// blockIdx.y
+__global__ void ref_assemble_kernel(int ns, int nt, int Q, const double* __restrict__ Ahat,
+                                    const double* __restrict__ G, const double* __restrict__ M,
+                                    const double* __restrict__ S, const double* __restrict__ theta, float* aug) {
+    const int n = ns * nt, g = blockIdx.y;
+    const double* th = theta + (int64_t)g * Q;
+    float* A = aug + (int64_t)g * n * 2 * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(t / n), col = (int)(t % n);
+        const int ip = row % ns, jp = row / ns, i = col % ns, j = col / ns;
+        double ah = 0.0;
+        for (int q = 0; q < Q; ++q) ah = fma(th[q], Ahat[(int64_t)q * ns * ns + ip + (int64_t)i * ns], ah);
+        double v = -ah * G[(int64_t)row + (int64_t)col * n];
+        if (ip == i) v += M[(int64_t)i * nt * nt + jp + (int64_t)j * nt] - S[(int64_t)i * nt * nt + jp + (int64_t)j * nt];
+        A[(int64_t)row * 2 * n + col] = (float)v;
+        A[(int64_t)row * 2 * n + n + col] = row == col ? 1.f : 0.f;
+    }
+}
+
+// Gauss-Jordan elimination with partial pivoting of [A | I] (one CTA per
+// reference): leaves A^{-1} in the right half.  A zero pivot sets *err.
+__global__ void __launch_bounds__(1024) gauss_jordan_kernel(int n, float* aug, int32_t* err) {
+    __shared__ float s_mult[4096];
+    __shared__ float s_v[32];
+    __shared__ int s_i[32];
+    __shared__ int s_piv;
+    float* A = aug + (int64_t)blockIdx.x * n * 2 * n;
+    const int ld = 2 * n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = 0; k < n; ++k) {
+        // pivot: largest |A[i][k]|, i >= k (smallest index on ties)
+        float best = -1.f;
+        int bi = n;
+        for (int i = k + tid; i < n; i += blockDim.x) {
+            const float v = fabsf(A[(int64_t)i * ld + k]);
+            if (v > best) {
+                best = v;
+                bi = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            s_v[warp] = best;
+            s_i[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float b = -1.f;
+            int p = n;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (s_v[w] > b || (s_v[w] == b && s_i[w] < p)) {
+                    b = s_v[w];
+                    p = s_i[w];
+                }
+            if (!(b > 0.f)) {
+                atomicCAS(reinterpret_cast<int*>(err), 0, ST_ERR_SINGULAR);
+                p = k;
+            }
+            s_piv = p;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        // swap rows k and p, then scale row k by 1 / pivot
+        if (p != k)
+            for (int c = tid; c < ld; c += blockDim.x) {
+                const float a = A[(int64_t)k * ld + c];
+                A[(int64_t)k * ld + c] = A[(int64_t)p * ld + c];
+                A[(int64_t)p * ld + c] = a;
+            }
+        __syncthreads();
+        const float piv = A[(int64_t)k * ld + k];
+        const float inv = piv != 0.f ? 1.f / piv : 0.f;
+        __syncthreads();
+        for (int c = tid; c < ld; c += blockDim.x) A[(int64_t)k * ld + c] *= inv;
+        for (int i = tid; i < n; i += blockDim.x) s_mult[i] = i == k ? 0.f : A[(int64_t)i * ld + k];
+        __syncthreads();
+        // eliminate column k from every other row: columns k .. 2n - 1 (the
+        // A part left of k is already zero there; with row exchanges the
+        // right half's nonzeros can sit in any column)
+        const int w = ld - k;
+        for (int64_t t = tid; t < (int64_t)n * w; t += blockDim.x) {
+            const int i = (int)(t / w), c = k + (int)(t % w);
+            const float mlt = s_mult[i];
+            if (mlt != 0.f) A[(int64_t)i * ld + c] = fmaf(-mlt, A[(int64_t)k * ld + c], A[(int64_t)i * ld + c]);
+        }
+        __syncthreads();
+    }
+}
+
+// P[g] (n x n, row major) = right half of aug[g]
+__global__ void ref_extract_kernel(int n, int n_ref, const float* __restrict__ aug, float* P) {
+    const int64_t tot = (int64_t)n_ref * n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = t / ((int64_t)n * n), rc = t % ((int64_t)n * n);
+        const int64_t r = rc / n, c = rc % n;
+        P[t] = aug[g * n * 2 * n + r * 2 * n + n + c];
+    }
+}
+
+// nearest reference of every sample (coordinates scaled by the references'
+// spread), and the per-reference counts
+__global__ void ref_assign_kernel(int n, const double* __restrict__ mu, int n_ref, const double* __restrict__ mu_ref,
+                                  double s0, double s1, int* grp, int* hist) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        double best = 1e300;
+        int bg = 0;
+        for (int g = 0; g < n_ref; ++g) {
+            const double d0 = (mu[2 * p] - mu_ref[2 * g]) * s0, d1 = (mu[2 * p + 1] - mu_ref[2 * g + 1]) * s1;
+            const double d = d0 * d0 + d1 * d1;
+            if (d < best) {
+                best = d;
+                bg = g;
+            }
+        }
+        grp[p] = bg;
+        atomicAdd(hist + bg, 1);
+    }
+}
+
+// sorted position of every sample: its reference's (tile-aligned) offset
+// plus a slot; perm maps sorted rows back to samples (-1 for padding)
+__global__ void ref_place_kernel(int n, const int* __restrict__ grp, const int* __restrict__ off, int* fill,
+                                 int* perm, int* pos) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int g = grp[p];
+        const int s = off[g] + atomicAdd(fill + g, 1);
+        perm[s] = p;
+        pos[p] = s;
+    }
+}
+
+// dst[pos[p]] = src[p] (rows of nf doubles), or the reverse
+__global__ void rows_move_kernel(int n, int nf, const int* __restrict__ pos, const double* __restrict__ src,
+                                 double* dst, int to_sorted) {
+    const int64_t tot = (int64_t)n * nf;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / nf, j = t % nf;
+        if (to_sorted) dst[(int64_t)pos[p] * nf + j] = src[t];
+        else dst[t] = src[(int64_t)pos[p] * nf + j];
+    }
+}
+
+// sorted row b: r = rhs - (K_0 x - sum_q theta_q K_q x) from the products C
+// (FP32 products combined in FP64), rel = ||r|| / ||rhs||; rows above the
+// gate are counted.  Padding rows give r = 0.
+__global__ void refine_residual_kernel(int rows, int n, int Q, const float* __restrict__ C, const int* __restrict__ perm,
+                                       const double* __restrict__ theta, const double* __restrict__ rhs, double gate,
+                                       double* Rs, double* rel, unsigned int* n_above) {
+    const int b = blockIdx.x;
+    if (b >= rows) return;
+    __shared__ double s_r[8], s_f[8];
+    const int p = perm[b];
+    double rr = 0.0, ff = 0.0;
+    const float* c = C + (int64_t)b * (Q + 1) * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double v = 0.0;
+        if (p >= 0) {
+            v = (double)c[j];
+            for (int q = 0; q < Q; ++q) v -= theta[(int64_t)p * Q + q] * (double)c[(int64_t)(q + 1) * n + j];
+            v = rhs[j] - v;
+        }
+        Rs[(int64_t)b * n + j] = v;
+        rr += v * v;
+        ff += rhs[j] * rhs[j];
+    }
+    rr = warp_sum(rr);
+    ff = warp_sum(ff);
+    if ((threadIdx.x & 31) == 0) {
+        s_r[threadIdx.x >> 5] = rr;
+        s_f[threadIdx.x >> 5] = ff;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, f = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += s_r[w];
+            f += s_f[w];
+        }
+        const double r = p < 0 ? 0.0 : (f > 0.0 ? sqrt(a / f) : sqrt(a));
+        rel[b] = r;
+        if (p >= 0 && !(r <= gate)) atomicAdd(n_above, 1u);
+    }
+}
+
+// X[b] += P_g R[b] for the sorted rows, g = the reference of the row's tile
+// (64 x 64 output tiles, FP32 products, FP64 accumulation into X)
+__global__ void __launch_bounds__(256) ref_correct_kernel(int rows, int n, const double* __restrict__ Rm,
+                                                          const float* __restrict__ P, const int* __restrict__ tile_ref,
+                                                          double* X) {
+    __shared__ float su[16][65];
+    __shared__ float sk[16][65];
+    const int b0 = blockIdx.y * kTile, r0 = blockIdx.x * kTile;
+    const float* K = P + (int64_t)tile_ref[blockIdx.y] * n * n;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < n; k0 += 16) {
+        for (int l = threadIdx.x; l < 64 * 16; l += 256) {
+            const int rr = l / 16, kk = l % 16;
+            su[kk][rr] = (b0 + rr < rows && k0 + kk < n) ? (float)Rm[(int64_t)(b0 + rr) * n + k0 + kk] : 0.f;
+            sk[kk][rr] = (r0 + rr < n && k0 + kk < n) ? K[(int64_t)(r0 + rr) * n + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], c[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = su[kk][ty + 16 * q];
+                c[q] = sk[kk][tx + 16 * q];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], c[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int b = b0 + ty + 16 * x, r = r0 + tx + 16 * y;
+            if (b < rows && r < n) X[(int64_t)b * n + r] += (double)acc[x][y];
+        }
+}
+
+// per sample: the final residual of its sorted row; 1 and a slot in the
+// fallback list when it is above the gate (or not finite)
+__global__ void refine_verdict_kernel(int n, const int* __restrict__ pos, const double* __restrict__ rel, double gate,
+                                      double* rel_res, int32_t* used, int* list, unsigned int* count) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const double r = rel[pos[p]];
+        const bool ok = isfinite(r) && r <= gate;
+        rel_res[p] = r;
+        used[p] = ok ? 0 : 1;
+        if (!ok) list[atomicAdd(count, 1u)] = p;
+    }
+}
+
+}  // namespace
+
+extern "C" st_status st_rom_precond_build(st_model* m, int32_t n_ref, const double* mu_ref, const double* theta_ref) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_rom_precond_build: NULL model");
+    if (!m->assembled) return st_fail(ST_ERR_STATE, "st_rom_precond_build: reduced operators not assembled");
+    if (n_ref < 1 || n_ref > 1024 || !mu_ref || !theta_ref) return st_fail(ST_ERR_ARG, "st_rom_precond_build: bad arguments");
+    const int n = m->ns * m->nt, Q = m->Q;
+    if (n > 4096) return st_fail(ST_ERR_ARG, "st_rom_precond_build: ns*nt = %d above 4096", n);
+    auto& P = m->prec;
+    P.n_ref = 0;
+    const size_t aug = (size_t)n_ref * n * 2 * n, inv = (size_t)n_ref * n * n;
+    ST_TRY(st_grow(m, P.work, sizeof(float) * aug + sizeof(double) * (size_t)n_ref * (Q + 2) + 256));
+    ST_TRY(st_grow(m, P.inv, sizeof(float) * inv));
+    float* d_aug = (float*)P.work.p;
+    double* d_theta = (double*)(d_aug + aug + (aug & 1));
+    cudaStream_t st = m->stream;
+    ST_CUDA_TRY(cudaMemcpyAsync(d_theta, theta_ref, sizeof(double) * n_ref * Q, cudaMemcpyHostToDevice, st));
+    {
+        ST_PROF(m, "precond_build_kernels");
+        const int gx = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 1024);
+        ref_assemble_kernel<<<dim3(gx, n_ref), 256, 0, st>>>(m->ns, m->nt, Q, m->d_Ahat, m->d_G, m->d_M, m->d_S,
+                                                             d_theta, d_aug);
+        ST_TRY(st_check_launch("precond assemble"));
+        gauss_jordan_kernel<<<n_ref, 1024, 0, st>>>(n, d_aug, m->d_err);
+        ST_TRY(st_check_launch("precond inverse"));
+        ref_extract_kernel<<<grid1d(m, (int64_t)inv), NT, 0, st>>>(n, n_ref, d_aug, (float*)P.inv.p);
+        ST_TRY(st_check_launch("precond extract"));
+    }
+    ST_TRY(st_sync(m));
+    P.mu.assign(mu_ref, mu_ref + 2 * (size_t)n_ref);
+    P.n_ref = n_ref;
+    P.n = n;
+    return ST_OK;
+}
+
+extern "C" st_status st_rom_refine(st_model* m, int32_t n, const double* mu, const double* theta, int32_t guess,
+                                   double gate, int32_t max_iter, double* uhat, double* rel_res,
+                                   int32_t* used_fallback, int32_t* iters_run, int32_t* n_fallback) {
+    if (!m) return st_fail(ST_ERR_ARG, "st_rom_refine: NULL model");
+    if (!m->assembled) return st_fail(ST_ERR_STATE, "st_rom_refine: reduced operators not assembled");
+    const int nf = m->ns * m->nt, Q = m->Q, R = (Q + 1) * nf;
+    auto& P = m->prec;
+    auto& s = m->mlp;
+    if (P.n_ref < 1 || P.n != nf) return st_fail(ST_ERR_STATE, "st_rom_refine: no preconditioner for this basis");
+    if (guess != ST_GUESS_SURROGATE && guess != ST_GUESS_ZERO) return st_fail(ST_ERR_ARG, "st_rom_refine: bad guess");
+    if (guess == ST_GUESS_SURROGATE && (!s.trained || s.n_out != nf))
+        return st_fail(ST_ERR_STATE, "st_rom_refine: no trained surrogate for this basis");
+    if (n < 0 || (n > 0 && (!mu || !theta || !uhat || !rel_res || !used_fallback)) || !(gate >= 0) || max_iter < 0)
+        return st_fail(ST_ERR_ARG, "st_rom_refine: bad arguments");
+    if (n == 0) {
+        if (n_fallback) *n_fallback = 0;
+        if (iters_run) *iters_run = 0;
+        return ST_OK;
+    }
+    cudaStream_t st = m->stream;
+    // 1. start: the surrogate's prediction, or zero
+    if (guess == ST_GUESS_SURROGATE) {
+        Views v = views(m);
+        const int chunk = 65536;
+        Acts a;
+        ST_TRY(acts(m, std::min(n, chunk), &a));
+        for (int b0 = 0; b0 < n; b0 += chunk) {
+            const int bb = std::min(chunk, n - b0);
+            gather_kernel<<<grid1d(m, bb), NT, 0, st>>>(bb, 0, bb, 1, 0, mu + 2 * (int64_t)b0, s.lo[0], s.lo[1],
+                                                        s.hi[0], s.hi[1], a.X, nullptr, 0, nf, nullptr, nullptr,
+                                                        nullptr);
+            ST_TRY(st_check_launch("refine gather"));
+            ST_TRY(forward(m, v, a, bb, false));
+            denorm_kernel<<<grid1d(m, (int64_t)bb * nf), NT, 0, st>>>(bb, nf, a.Y, v.mean, v.stdv,
+                                                                      uhat + (int64_t)b0 * nf, nf);
+            ST_TRY(st_check_launch("refine denorm"));
+        }
+    } else {
+        ST_CUDA_TRY(cudaMemsetAsync(uhat, 0, sizeof(double) * (size_t)n * nf, st));
+    }
+    // 2. the affine pieces of Ahat^st
+    ST_TRY(st_grow(m, s.kall, sizeof(float) * (size_t)R * nf));
+    kall_kernel<<<grid1d(m, (int64_t)R * nf), NT, 0, st>>>(m->ns, m->nt, Q, m->d_Ahat, m->d_G, m->d_M, m->d_S,
+                                                           (float*)s.kall.p);
+    ST_TRY(st_check_launch("refine kall"));
+    // 3. samples sorted by nearest reference, each reference's rows padded to
+    //    whole tiles
+    const int nr = P.n_ref;
+    double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+    for (int g = 0; g < nr; ++g)
+        for (int c = 0; c < 2; ++c) {
+            lo[c] = std::min(lo[c], P.mu[2 * g + c]);
+            hi[c] = std::max(hi[c], P.mu[2 * g + c]);
+        }
+    const double sc0 = hi[0] > lo[0] ? 1.0 / (hi[0] - lo[0]) : 1.0, sc1 = hi[1] > lo[1] ? 1.0 / (hi[1] - lo[1]) : 1.0;
+    const int64_t rows_max = (int64_t)n + (int64_t)nr * kTile;
+    const size_t ints = (size_t)2 * n + rows_max + 3 * (size_t)nr + (size_t)rows_max / kTile + 64;
+    const size_t dbl = (size_t)rows_max * nf * 2 + rows_max + 2 * (size_t)nr;
+    const size_t flt = (size_t)rows_max * R;
+    ST_TRY(st_grow(m, m->ws_misc, sizeof(double) * dbl + sizeof(float) * flt + sizeof(int) * ints + 1024));
+    double* Xs = (double*)m->ws_misc.p;
+    double* Rs = Xs + (size_t)rows_max * nf;
+    double* rel = Rs + (size_t)rows_max * nf;
+    double* d_mur = rel + rows_max;
+    float* C = (float*)(d_mur + 2 * (size_t)nr);
+    int* grp = (int*)(C + flt);
+    int* pos = grp + n;
+    int* perm = pos + n;
+    int* hist = perm + rows_max;
+    int* off = hist + nr;
+    int* fill = off + nr;
+    int* tile_ref = fill + nr;
+    unsigned int* cnt = (unsigned int*)(tile_ref + rows_max / kTile + 8);
+    ST_CUDA_TRY(cudaMemcpyAsync(d_mur, P.mu.data(), sizeof(double) * 2 * nr, cudaMemcpyHostToDevice, st));
+    ST_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * 2 * nr + sizeof(int) * nr, st));
+    ref_assign_kernel<<<grid1d(m, n), NT, 0, st>>>(n, mu, nr, d_mur, sc0, sc1, grp, hist);
+    ST_TRY(st_check_launch("refine assign"));
+    std::vector<int> h_hist(nr), h_off(nr), h_tiles;
+    ST_CUDA_TRY(cudaMemcpyAsync(h_hist.data(), hist, sizeof(int) * nr, cudaMemcpyDeviceToHost, st));
+    ST_CUDA_TRY(cudaStreamSynchronize(st));
+    int rows = 0;
+    for (int g = 0; g < nr; ++g) {
+        h_off[g] = rows;
+        const int t = (h_hist[g] + kTile - 1) / kTile;
+        for (int i = 0; i < t; ++i) h_tiles.push_back(g);
+        rows += t * kTile;
+    }
+    ST_CUDA_TRY(cudaMemcpyAsync(off, h_off.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    ST_CUDA_TRY(cudaMemcpyAsync(tile_ref, h_tiles.data(), sizeof(int) * h_tiles.size(), cudaMemcpyHostToDevice, st));
+    ST_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int) * nr, st));
+    ST_CUDA_TRY(cudaMemsetAsync(perm, 0xff, sizeof(int) * rows, st));
+    ref_place_kernel<<<grid1d(m, n), NT, 0, st>>>(n, grp, off, fill, perm, pos);
+    ST_TRY(st_check_launch("refine place"));
+    ST_CUDA_TRY(cudaMemsetAsync(Xs, 0, sizeof(double) * (size_t)rows * nf, st));
+    rows_move_kernel<<<grid1d(m, (int64_t)n * nf), NT, 0, st>>>(n, nf, pos, uhat, Xs, 1);
+    ST_TRY(st_check_launch("refine to sorted"));
+    // 4. residual, then correction, until every row meets the gate
+    int it = 0;
+    for (;; ++it) {
+        {
+            ST_PROF(m, "gate_gemm_kernel");
+            gate_gemm_kernel<<<dim3((R + 63) / 64, (rows + 63) / 64), 256, 0, st>>>(rows, R, nf, Xs, nf,
+                                                                                   (float*)s.kall.p, C);
+            ST_TRY(st_check_launch("refine residual products"));
+        }
+        ST_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
+        refine_residual_kernel<<<rows, 128, 0, st>>>(rows, nf, Q, C, perm, theta, m->d_rhs, gate, Rs, rel, cnt);
+        ST_TRY(st_check_launch("refine residual"));
+        unsigned int above = 0;
+        ST_CUDA_TRY(cudaMemcpyAsync(&above, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        ST_CUDA_TRY(cudaStreamSynchronize(st));
+        if (above == 0 || it >= max_iter) break;
+        ST_PROF(m, "precond_correct_kernel");
+        ref_correct_kernel<<<dim3((nf + kTile - 1) / kTile, rows / kTile), 256, 0, st>>>(rows, nf, Rs,
+                                                                                      (const float*)P.inv.p,
+                                                                                      tile_ref, Xs);
+        ST_TRY(st_check_launch("refine correction"));
+    }
+    if (iters_run) *iters_run = it;
+    // 5. back to the samples' order; the gate's verdict; LU for the rest
+    rows_move_kernel<<<grid1d(m, (int64_t)n * nf), NT, 0, st>>>(n, nf, pos, Xs, uhat, 0);
+    ST_TRY(st_check_launch("refine from sorted"));
+    ST_TRY(st_grow(m, s.list, sizeof(int) * (size_t)n + 64));
+    int* list = (int*)s.list.p;
+    unsigned int* lcount = (unsigned int*)(list + n);
+    ST_CUDA_TRY(cudaMemsetAsync(lcount, 0, sizeof(unsigned int), st));
+    refine_verdict_kernel<<<grid1d(m, n), NT, 0, st>>>(n, pos, rel, gate, rel_res, used_fallback, list, lcount);
+    ST_TRY(st_check_launch("refine verdict"));
+    unsigned int hc = 0;
+    ST_CUDA_TRY(cudaMemcpyAsync(&hc, lcount, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    ST_CUDA_TRY(cudaStreamSynchronize(st));
+    if (n_fallback) *n_fallback = (int32_t)hc;
+    return st_internal_solve_list(m, (int)hc, list, theta, uhat, rel_res, nullptr);
+}

@@ -266,7 +266,7 @@ void st_model_destroy(st_model* m) {
     cudaFree(m->d_bar);
     if (m->adj) st_model_destroy(m->adj);
     for (DevBuf* b : {&m->W, &m->V, &m->ws_fom, &m->ws_pod, &m->ws_pod2, &m->ws_gemm, &m->ws_oz,
-                      &m->ws_solve, &m->ws_misc, &m->ws_srom, &m->ws_cert, &m->mlp.params, &m->mlp.grad, &m->mlp.adam_m,
+                      &m->ws_solve, &m->ws_misc, &m->ws_srom, &m->ws_cert, &m->prec.inv, &m->prec.work, &m->mlp.params, &m->mlp.grad, &m->mlp.adam_m,
                       &m->mlp.adam_v, &m->mlp.wbf, &m->mlp.stats, &m->mlp.act, &m->mlp.kall,
                       &m->mlp.list})
         cudaFree(b->p);
