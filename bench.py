@@ -55,9 +55,9 @@ ONLINE_REFINE = 3
 # kernels, scaled to a launch by the units it processes (the captures and
 # their commands are summarised under profiles/)
 NCU_DRAM_BYTES = {
-    # profiles/fom_march_kernel_c4_16mu_10steps.md: 140.6 MB + 222.4 MB for 10
-    # steps of the 16-parameter march; per step of the march
-    "fom_march_kernel": {"per": "step", "bytes": (140.625152e6 + 222.354176e6) / 10},
+    # profiles/fom_march_kernel_c4_16mu_10steps_subgrids.md: 141.0 MB + 317.0 MB
+    # for 10 steps of the 16-parameter march in 8 sub-grids; per step of the march
+    "fom_march_kernel": {"per": "step", "bytes": (141.030656e6 + 316.994816e6) / 10},
 }
 # dependence threshold of the incremental SVD, relative to the block's largest
 # column: the value of the paper's first numerical example (Sec. 6); the

@@ -18,7 +18,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Counting grid barrier for cooperative launches (all blocks are
-// co-resident, so every arrival happens).  The wait is bounded: after
+// co-resident, so every arrival happens), over the whole grid or over the
+// `parties` CTAs of one sub-grid that share the counters.  The wait is bounded: after
 // `limit` polls the waiting block records ST_ERR_TIMEOUT in the model error
 // word, raises the launch's abort flag and the barrier reports failure, so
 // every block returns instead of hanging.  count/gen/abort are zeroed by the
@@ -29,6 +30,7 @@ struct GridBarrier {
     unsigned int* abort;
     int32_t* err;
     long long limit;
+    unsigned int parties;  // CTAs that take part; 0 = the whole grid
 };
 
 __device__ __forceinline__ void grid_abort(const GridBarrier& b, int32_t code) {
@@ -70,7 +72,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b, int* s_flag) {
         const unsigned int my = ld_acquire_gpu(b.gen);
         const unsigned int arrived = atom_add_acq_rel_gpu(b.count, 1u);
         int ok = 1;
-        if (arrived == gridDim.x - 1) {
+        if (arrived == (b.parties ? b.parties : gridDim.x) - 1) {
             st_relaxed_gpu(b.count, 0u);
             red_release_gpu(b.gen, 1u);
         } else {

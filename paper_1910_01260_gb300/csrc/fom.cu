@@ -74,7 +74,11 @@ struct FomArgs {
     int32_t* status;
     double tol;
     int maxit;
-    GridBarrier bar;
+    GridBarrier bar;  // counters of sub-grid 0; sub-grid s uses count/gen/abort + 4 s
+    // sub-grids: CTAs [s * per, (s + 1) * per) march samples [s * per_sub, ...)
+    // of the group, with workspace (amu, vectors, partials) at + s * sub_doubles
+    int per, per_sub;
+    int64_t sub_doubles;
 };
 
 template <int LD>
@@ -165,7 +169,7 @@ __device__ __forceinline__ void spmv_A(const FomArgs& a, int64_t row, int p0, co
 // partial sums.
 template <int LD, int NS>
 __device__ __forceinline__ void block_partial(double (&c)[NS][Cfg<LD>::VEC], double* partial,
-                                              double (*s_warp)[NSLOT][LD]) {
+                                              double (*s_warp)[NSLOT][LD], int bid) {
     constexpr int VEC = Cfg<LD>::VEC, LPR = Cfg<LD>::LPR, NW = Cfg<LD>::NW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -183,19 +187,19 @@ __device__ __forceinline__ void block_partial(double (&c)[NS][Cfg<LD>::VEC], dou
         double acc = 0.0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) acc += s_warp[w][sl][p];
-        __stcg(partial + ((int64_t)blockIdx.x * NS + sl) * LD + p, acc);
+        __stcg(partial + ((int64_t)bid * NS + sl) * LD + p, acc);
     }
 }
 
 // Fixed-order sum of all blocks' partials (run by every block).
 template <int LD, int NS>
-__device__ __forceinline__ void grid_reduce(const double* partial, double (*s_red)[LD]) {
+__device__ __forceinline__ void grid_reduce(const double* partial, double (*s_red)[LD], int nblk) {
     constexpr int NW = Cfg<LD>::NW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = warp; q < NS * LD; q += NW) {
         const int sl = q / LD, p = q % LD;
         double acc = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32)
+        for (int b = lane; b < nblk; b += 32)
             acc += __ldcg(partial + ((int64_t)b * NS + sl) * LD + p);
         acc = warp_sum(acc);
         if (lane == 0) s_red[sl][p] = acc;
@@ -205,8 +209,42 @@ __device__ __forceinline__ void grid_reduce(const double* partial, double (*s_re
 
 // SRC: the right-hand side of step k also carries a per-sample vector z_k
 // (a general source, as in the space-time system A^st u = z).
+// One cooperative launch holds several independent sub-grids of `per` CTAs:
+// sub-grid s marches its own samples with its own barrier counters and
+// partials (fewer arrivals per barrier, fewer partials per reduction, and no
+// lock step between the sub-grids' samples).  The sub-grid's view of the
+// arguments is made once at entry.
+constexpr int kMaxSub = 8;
+
 template <int LD, bool SRC>
-__global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(FomArgs a) {
+__global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(FomArgs A) {
+    const int sub = blockIdx.x / A.per;
+    const int bid = blockIdx.x - sub * A.per, nblk = A.per;
+    FomArgs a = A;
+    {
+        const int p0 = sub * A.per_sub;
+        const size_t off = (size_t)sub * A.sub_doubles;
+        a.n_mu = min(A.per_sub, A.n_mu - p0);
+        a.theta = A.theta + (size_t)p0 * A.Q;
+        a.amu = A.amu + off;
+        a.x = A.x + off;
+        a.r = A.r + off;
+        a.rh = A.rh + off;
+        a.p = A.p + off;
+        a.v = A.v + off;
+        a.s = A.s + off;
+        a.t = A.t + off;
+        a.hist = A.hist + off;
+        a.partial = A.partial + off;
+        a.snap = A.snap + (size_t)p0 * A.Nt * A.N;
+        a.src = A.src ? A.src + (size_t)p0 * A.Nt * A.N : nullptr;
+        a.iters = A.iters ? A.iters + (size_t)A.Nt * p0 : nullptr;
+        a.status = A.status ? A.status + p0 : nullptr;
+        a.bar.count = A.bar.count + 4 * sub;
+        a.bar.gen = A.bar.gen + 4 * sub;
+        a.bar.abort = A.bar.abort + 4 * sub;
+        a.bar.parties = (unsigned int)A.per;
+    }
     using C = Cfg<LD>;
     constexpr int VEC = C::VEC, LPR = C::LPR, RPB = C::RPB, NW = C::NW;
     __shared__ double s_warp[NW][NSLOT][LD];
@@ -236,11 +274,11 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
     // summing the previous ones; a buffer is rewritten only two barriers
     // after it was read.
     int red = 0;
-    const size_t part_stride = (size_t)gridDim.x * NSLOT * LD;
+    const size_t part_stride = (size_t)nblk * NSLOT * LD;
 #define PART (a.partial + (size_t)(red & 1) * part_stride)
 
 #define ROWS_BEGIN                                                                    \
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {                   \
+    for (int64_t ch = bid; ch < nchunks; ch += nblk) {                               \
         const int64_t row = ch * RPB + rb;                                            \
         if (row >= N) continue;                                                       \
         const int64_t vi = row * LD + p0;
@@ -316,10 +354,10 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
                 st_vec<VEC>(a.p + vi, zero);
                 st_vec<VEC>(a.v + vi, zero);
             ROWS_END
-            block_partial<LD, 2>(c, PART, s_warp);
+            block_partial<LD, 2>(c, PART, s_warp, bid);
         }
         if (!grid_sync(a.bar, &s_flag)) return;
-        grid_reduce<LD, 2>(PART, s_red);
+        grid_reduce<LD, 2>(PART, s_red, nblk);
         ++red;
         if (threadIdx.x < LD) {
             const int p = threadIdx.x;
@@ -399,10 +437,10 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
                         }
                     st_vec<VEC>(a.v + vi, vv);
                 ROWS_END
-                block_partial<LD, 1>(c, PART, s_warp);
+                block_partial<LD, 1>(c, PART, s_warp, bid);
             }
             if (!grid_sync(a.bar, &s_flag)) return;
-            grid_reduce<LD, 1>(PART, s_red);
+            grid_reduce<LD, 1>(PART, s_red, nblk);
             ++red;
             if (threadIdx.x < LD) {
                 const int p = threadIdx.x;
@@ -438,10 +476,10 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
                         }
                     st_vec<VEC>(a.s + vi, sv);
                 ROWS_END
-                block_partial<LD, 1>(c, PART, s_warp);
+                block_partial<LD, 1>(c, PART, s_warp, bid);
             }
             if (!grid_sync(a.bar, &s_flag)) return;
-            grid_reduce<LD, 1>(PART, s_red);
+            grid_reduce<LD, 1>(PART, s_red, nblk);
             ++red;
             if (threadIdx.x < LD) {
                 const int p = threadIdx.x;
@@ -482,10 +520,10 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
                     st_vec<VEC>(a.t + vi, tv);
                     st_vec<VEC>(a.x + vi, xv);
                 ROWS_END
-                block_partial<LD, 2>(c, PART, s_warp);
+                block_partial<LD, 2>(c, PART, s_warp, bid);
             }
             if (!grid_sync(a.bar, &s_flag)) return;
-            grid_reduce<LD, 2>(PART, s_red);
+            grid_reduce<LD, 2>(PART, s_red, nblk);
             ++red;
             if (threadIdx.x < LD) {
                 const int p = threadIdx.x;
@@ -530,10 +568,10 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
                     st_vec<VEC>(a.x + vi, xv);
                     st_vec<VEC>(a.r + vi, rv);
                 ROWS_END
-                block_partial<LD, 2>(c, PART, s_warp);
+                block_partial<LD, 2>(c, PART, s_warp, bid);
             }
             if (!grid_sync(a.bar, &s_flag)) return;
-            grid_reduce<LD, 2>(PART, s_red);
+            grid_reduce<LD, 2>(PART, s_red, nblk);
             ++red;
             if (threadIdx.x < LD) {
                 const int p = threadIdx.x;
@@ -572,7 +610,7 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
             if (changed) st_vec<VEC>(a.x + vi, xv);
             st_vec<VEC>(a.hist + (size_t)((k + 1) % kHist) * vecsz + vi, xv);
         ROWS_END
-        if (blockIdx.x == 0 && threadIdx.x < a.n_mu) {
+        if (bid == 0 && threadIdx.x < a.n_mu) {
             const int p = threadIdx.x;
             if (a.iters) a.iters[(int64_t)k * a.n_mu + p] = s_it[p];
         }
@@ -580,7 +618,7 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
         if (threadIdx.x < LD && s_state[threadIdx.x] == S_ZERO) s_state[threadIdx.x] = S_CONV;
         __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x < a.n_mu) {
+    if (bid == 0 && threadIdx.x < a.n_mu) {
         const int p = threadIdx.x;
         if (a.status) a.status[p] = s_code[p];
         if (s_code[p] != ST_OK) st_dev_error(a.bar.err, s_code[p]);
@@ -1127,8 +1165,23 @@ st_status run_cluster(st_model* m, int n_mu, const double* d_theta, int Nt, cons
     return st_check_launch("fom_cluster");
 }
 
+// Sub-grids per launch for a group of n_mu samples: two samples per
+// sub-grid, at most kMaxSub (ST_FOM_SUBGRIDS fixes the count).  Measured on
+// the c4 march of 16 samples (200 steps): 1, 2, 4, 8, 16 sub-grids take
+// 97.5, 86.5, 82.5, 80.0, 92.5 ms -- with one sample per sub-grid the shared
+// operator is read once per sample and the loads are 8 bytes.
+#ifndef ST_FOM_SUBGRIDS
+#define ST_FOM_SUBGRIDS 0
+#endif
+int fom_subgrids(int n_mu) {
+    if (ST_FOM_SUBGRIDS > 0) return std::min(ST_FOM_SUBGRIDS, std::min(kMaxSub, n_mu));
+    return std::max(1, std::min(kMaxSub, n_mu / 2));
+}
+
+// March n_mu samples (at most n_sub * LD) in one cooperative launch of n_sub
+// sub-grids; sub-grid s takes samples [s * per_sub, ...).
 template <int LD>
-st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const double* d_dt,
+st_status run_group(st_model* m, int n_mu, int n_sub, const double* d_theta, int Nt, const double* d_dt,
                     const double* u0, int n_in, const double* B, const double* d_F, const double* src,
                     double* snap, int32_t* iters, int32_t* status, int32_t* d_iters_tmp) {
     const int64_t N = m->N, ell = m->ell_size, mx = m->mx_size;
@@ -1136,25 +1189,33 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     const void* kern = src ? (const void*)fom_march_kernel<LD, true> : (const void*)fom_march_kernel<LD, false>;
     int blocks = st_coop_blocks(m, fom_march_kernel<LD, false>, NT, 0, ST_FOM_BLOCKS_PER_SM);
     if (src) blocks = std::min(blocks, st_coop_blocks(m, fom_march_kernel<LD, true>, NT, 0, ST_FOM_BLOCKS_PER_SM));
-    if (blocks < 1) return st_fail(ST_ERR_CUDA, "fom: cooperative occupancy query failed");
+    if (blocks < n_sub) return st_fail(ST_ERR_CUDA, "fom: cooperative occupancy query failed");
     const int64_t rpb = Cfg<LD>::RPB;
     const int64_t nchunks = (N + rpb - 1) / rpb;
-    if (blocks > nchunks) blocks = (int)std::max<int64_t>(1, nchunks);
-    size_t need = sizeof(double) * ((size_t)mx * LD + (7 + kHist) * vec + 2 * (size_t)blocks * NSLOT * LD) + 1024;
+    int per = blocks / n_sub;
+    if (per > nchunks) per = (int)std::max<int64_t>(1, nchunks);
+    const int per_sub = (n_mu + n_sub - 1) / n_sub;
+    const size_t sub_doubles = (size_t)mx * LD + (7 + kHist) * vec + 2 * (size_t)per * NSLOT * LD;
+    const size_t need = sizeof(double) * (sub_doubles * n_sub) + sizeof(unsigned int) * 4 * kMaxSub + 1024;
     ST_TRY(st_grow(m, m->ws_fom, need));
+    unsigned int* bars = (unsigned int*)((double*)m->ws_fom.p + sub_doubles * n_sub);
+    ST_CUDA_TRY(cudaMemsetAsync(bars, 0, sizeof(unsigned int) * 4 * kMaxSub, m->stream));
+    FomArgs a;
     double* base = (double*)m->ws_fom.p;
+    for (int sb = 0; sb < n_sub; ++sb) {
+        const int p0 = sb * per_sub, ng = std::max(0, std::min(per_sub, n_mu - p0));
+        double* amu = base + sub_doubles * sb;
+        if (ng > 0) {
+            int sblocks = (int)std::min<int64_t>((std::max(mx, N) * LD + 255) / 256, 8 * m->num_sms);
+            ST_PROF(m, "fom_setup_kernel");
+            fom_setup_kernel<LD><<<std::max(sblocks, 1), 256, 0, m->stream>>>(
+                mx, m->d_mx_src, ell, m->Q, m->d_vals, d_theta + (size_t)p0 * m->Q, ng, amu, N, u0,
+                amu + (size_t)mx * LD);
+            ST_TRY(st_check_launch("fom_setup"));
+        }
+    }
     double* amu = base;
     double* vecs = amu + (size_t)mx * LD;
-    double* partial = vecs + (7 + kHist) * vec;
-    int sblocks = (int)std::min<int64_t>((std::max(mx, N) * LD + 255) / 256, 8 * m->num_sms);
-    {
-        ST_PROF(m, "fom_setup_kernel");
-        fom_setup_kernel<LD><<<std::max(sblocks, 1), 256, 0, m->stream>>>(
-            mx, m->d_mx_src, ell, m->Q, m->d_vals, d_theta, n_mu, amu, N, u0, vecs);
-        ST_TRY(st_check_launch("fom_setup"));
-    }
-    ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, m->stream));
-    FomArgs a;
     a.N = N;
     a.Q = m->Q;
     a.theta = d_theta;
@@ -1180,18 +1241,21 @@ st_status run_group(st_model* m, int n_mu, const double* d_theta, int Nt, const 
     a.s = vecs + 5 * vec;
     a.t = vecs + 6 * vec;
     a.hist = vecs + 7 * vec;
-    a.partial = partial;
+    a.partial = vecs + (7 + kHist) * vec;
     a.snap = snap;
     a.n_mu = n_mu;
     a.iters = iters ? d_iters_tmp : nullptr;
     a.status = status;
     a.tol = m->opt.tol;
     a.maxit = m->opt.maxit;
-    a.bar = GridBarrier{m->d_bar, m->d_bar + 1, m->d_bar + 2, m->d_err, m->opt.spin_limit};
+    a.bar = GridBarrier{bars, bars + 1, bars + 2, m->d_err, m->opt.spin_limit, (unsigned int)per};
+    a.per = per;
+    a.per_sub = per_sub;
+    a.sub_doubles = (int64_t)sub_doubles;
     void* args[] = {&a};
     ST_PROF(m, "fom_march_kernel");
-    ST_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(NT), args, 0, m->stream));
-        st_count_launch();
+    ST_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(per * n_sub), dim3(NT), args, 0, m->stream));
+    st_count_launch();
     return ST_OK;
 }
 
@@ -1244,27 +1308,32 @@ st_status st_internal_fom_march(st_model* m, int32_t n_mu, const double* theta, 
     }
     for (int g0 = 0; g0 < n_mu; g0 += 32) {
         const int ng = std::min(32, n_mu - g0);
+        const int per_sub = (ng + fom_subgrids(ng) - 1) / fom_subgrids(ng);
+        const int n_sub = (ng + per_sub - 1) / per_sub;  // no empty sub-grid
         int ld = 1;
-        while (ld < ng) ld <<= 1;
+        while (ld < per_sub) ld <<= 1;
         double* snap = snapshots + (size_t)g0 * Nt * m->N;
         int32_t* st = status ? status + g0 : nullptr;
         const double* th = d_theta + (size_t)g0 * Q;
         const double* sg = src ? src + (size_t)g0 * Nt * m->N : nullptr;
         st_status rc;
         switch (ld) {
-            case 1: rc = run_group<1>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
-            case 2: rc = run_group<2>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
-            case 4: rc = run_group<4>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
-            case 8: rc = run_group<8>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
-            case 16: rc = run_group<16>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
-            default: rc = run_group<32>(m, ng, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 1: rc = run_group<1>(m, ng, n_sub, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 2: rc = run_group<2>(m, ng, n_sub, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 4: rc = run_group<4>(m, ng, n_sub, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 8: rc = run_group<8>(m, ng, n_sub, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            case 16: rc = run_group<16>(m, ng, n_sub, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
+            default: rc = run_group<32>(m, ng, n_sub, th, Nt, d_dt, u0, n_in, B, d_F, sg, snap, iters, st, d_it); break;
         }
         if (rc != ST_OK) return rc;
         if (iters) {
-            // group counts [Nt x ng] -> caller layout [Nt x n_mu]
-            ST_CUDA_TRY(cudaMemcpy2DAsync(iters + g0, sizeof(int32_t) * n_mu, d_it,
-                                          sizeof(int32_t) * ng, sizeof(int32_t) * ng, Nt,
-                                          cudaMemcpyDeviceToDevice, m->stream));
+            // each sub-grid's counts [Nt x its samples] -> caller layout [Nt x n_mu]
+            for (int p0 = 0; p0 < ng; p0 += per_sub) {
+                const int c = std::min(per_sub, ng - p0);
+                ST_CUDA_TRY(cudaMemcpy2DAsync(iters + g0 + p0, sizeof(int32_t) * n_mu, d_it + (size_t)Nt * p0,
+                                              sizeof(int32_t) * c, sizeof(int32_t) * c, Nt,
+                                              cudaMemcpyDeviceToDevice, m->stream));
+            }
         }
     }
     return ST_OK;
