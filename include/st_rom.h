@@ -552,6 +552,10 @@ st_status st_rom_surrogate_train(st_model* m, int32_t n, const double* mu, const
  * prediction is accepted if ||Ahat^st(mu) uhat - rhs|| / ||rhs|| <= gate
  * (evaluated in FP32 from the affine pieces of Ahat^st, Eq. ij-block-matrix),
  * otherwise the sample is solved by the batched FP64 LU of st_rom_solve.
+ * The residual's products run on the tensor cores when ns*nt is a multiple of
+ * 4: both operands split into three BF16 parts (8 bits each), the six cross
+ * products of order <= 4 summed in FP32 by one BF16 GEMM (FP32-accurate);
+ * otherwise in FP32 on the SIMT cores.
  *   mu dev [n x 2], theta dev [n x Q] (same samples), uhat dev [n x ns*nt]
  *   rel_res dev [n]: gate residual, or the LU residual for fallback samples
  *   used_fallback dev [n]: 1 where the LU was used
@@ -575,8 +579,8 @@ st_status st_rom_precond_build(st_model* m, int32_t n_ref, const double* mu_ref,
  *   x <- x + P_g (fhat^st - Ahat^st(mu) x),  P_g = Ahat^st(mu_g)^{-1},
  * with mu_g the reference nearest to mu (coordinates scaled by the
  * references' spread).  Every step evaluates the residual of the whole batch
- * through the affine pieces of Ahat^st (FP32 products combined in FP64, as
- * the surrogate's gate) and stops as soon as every sample satisfies
+ * through the affine pieces of Ahat^st (FP32-accurate products -- on the
+ * tensor cores as for the surrogate's gate -- combined in FP64) and stops as soon as every sample satisfies
  * ||rhs - Ahat^st x|| / ||rhs|| <= gate, or after max_iter corrections;
  * samples still above the gate are then solved by the batched LU of
  * st_rom_solve (their rel_res is the LU's).  Full (ns, nt) only.  The

@@ -145,6 +145,7 @@ struct st_model {
         int64_t adam_t = 0;
         double lo[2] = {0, 0}, hi[2] = {1, 1};
         DevBuf params, grad, adam_m, adam_v, wbf, stats, act, kall, list;
+        DevBuf kall16, xsplit;  // BF16 three-part splits for the tensor-core residual product
     } mlp;
 };
 

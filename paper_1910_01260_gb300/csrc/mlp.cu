@@ -578,6 +578,13 @@ extern "C" st_status st_rom_surrogate_train(st_model* m, int32_t n, const double
     return ST_OK;
 }
 
+namespace {
+// the tensor-core residual products (defined with the refinement below)
+bool tc_residual_ok(const st_model* m);
+st_status residual_prepare(st_model* m);
+st_status residual_products(st_model* m, int rows, const double* X, int ldx, float* C);
+}  // namespace
+
 extern "C" st_status st_rom_surrogate_infer(st_model* m, int32_t n, const double* mu, const double* theta, double gate,
                                             double* uhat, double* rel_res, int32_t* used_fallback, int32_t* n_fallback) {
     if (!m) return st_fail(ST_ERR_ARG, "st_rom_surrogate_infer: NULL model");
@@ -595,11 +602,17 @@ extern "C" st_status st_rom_surrogate_infer(st_model* m, int32_t n, const double
     const int R = (Q + 1) * n_out;
     cudaStream_t st = m->stream;
     Views v = views(m);
-    // gate operator
-    ST_TRY(st_grow(m, s.kall, sizeof(float) * (size_t)R * n_out));
-    kall_kernel<<<grid1d(m, (int64_t)R * n_out), NT, 0, st>>>(m->ns, m->nt, Q, m->d_Ahat, m->d_G, m->d_M, m->d_S,
-                                                             (float*)s.kall.p);
-    ST_TRY(st_check_launch("mlp kall"));
+    // gate operator: the affine pieces of Ahat^st (three-part BF16 splits for
+    // the tensor-core products, or FP32 for the SIMT ones)
+    const bool tc = tc_residual_ok(m);
+    if (tc) {
+        ST_TRY(residual_prepare(m));
+    } else {
+        ST_TRY(st_grow(m, s.kall, sizeof(float) * (size_t)R * n_out));
+        kall_kernel<<<grid1d(m, (int64_t)R * n_out), NT, 0, st>>>(m->ns, m->nt, Q, m->d_Ahat, m->d_G, m->d_M,
+                                                                 m->d_S, (float*)s.kall.p);
+        ST_TRY(st_check_launch("mlp kall"));
+    }
     const int chunk = 65536;
     ST_TRY(st_grow(m, s.list, sizeof(int) * (size_t)n + 64));
     int* list = (int*)s.list.p;
@@ -618,7 +631,9 @@ extern "C" st_status st_rom_surrogate_infer(st_model* m, int32_t n, const double
         denorm_kernel<<<grid1d(m, (int64_t)bb * n_out), NT, 0, st>>>(bb, n_out, a.Y, v.mean, v.stdv,
                                                                      uhat + (int64_t)b0 * n_out, n_out);
         ST_TRY(st_check_launch("mlp denorm"));
-        {
+        if (tc) {
+            ST_TRY(residual_products(m, bb, uhat + (int64_t)b0 * n_out, n_out, C));
+        } else {
             ST_PROF(m, "gate_gemm_kernel");
             gate_gemm_kernel<<<dim3((R + 63) / 64, (bb + 63) / 64), 256, 0, st>>>(
                 bb, R, n_out, uhat + (int64_t)b0 * n_out, n_out, (float*)s.kall.p, C);
@@ -959,6 +974,95 @@ __global__ void __launch_bounds__(256) ref_correct_kernel(int rows, int n, const
         }
 }
 
+// ---- the residual products on the tensor cores ------------------------------
+// C = X K_all^T with both operands split into three BF16 parts, x = x1 + x2 +
+// x3 (8 significant bits each, x2 and x3 the rounded remainders), and the six
+// cross products with i + j <= 4 accumulated in FP32 by one BF16 GEMM over
+// the concatenated K: A' = [x1 x1 x1 x2 x2 x3], B' = [k1 k2 k3 k1 k2 k1].  The
+// products are as accurate as FP32 ones (the dropped terms are 2^-24 of the
+// product); the GEMM is the tcgen05 kernel of the surrogate.
+
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+    a = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(a);
+    b = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(b);
+    c = __double2bfloat16(r2);
+}
+
+// A'[b] = [x1 x1 x1 x2 x2 x3] for the rows of X (rows x n, ld ldx)
+__global__ void split_rows_kernel(int rows, int n, const double* __restrict__ X, int ldx, __nv_bfloat16* A) {
+    const int64_t tot = (int64_t)rows * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = t / n, k = t % n;
+        __nv_bfloat16 x1, x2, x3;
+        split3(X[b * ldx + k], x1, x2, x3);
+        __nv_bfloat16* a = A + b * 6 * n + k;
+        a[0] = x1;
+        a[n] = x1;
+        a[2 * n] = x1;
+        a[3 * n] = x2;
+        a[4 * n] = x2;
+        a[5 * n] = x3;
+    }
+}
+
+// B'[r] = [k1 k2 k3 k1 k2 k1] for the rows r of K_all (the affine pieces of
+// Ahat^st, formed in FP64 as in kall_kernel)
+__global__ void kall_split_kernel(int ns, int nt, int Q, const double* __restrict__ Ahat, const double* __restrict__ G,
+                                  const double* __restrict__ M, const double* __restrict__ S, __nv_bfloat16* Bp) {
+    const int n = ns * nt;
+    const int64_t tot = (int64_t)(Q + 1) * n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t / ((int64_t)n * n));
+        const int64_t rc = t % ((int64_t)n * n);
+        const int row = (int)(rc / n), col = (int)(rc % n);
+        const int ip = row % ns, jp = row / ns, i = col % ns, j = col / ns;
+        double v;
+        if (q == 0) {
+            v = (ip == i) ? M[(int64_t)i * nt * nt + jp + (int64_t)j * nt] - S[(int64_t)i * nt * nt + jp + (int64_t)j * nt] : 0.0;
+        } else {
+            v = Ahat[(int64_t)(q - 1) * ns * ns + ip + (int64_t)i * ns] * G[(int64_t)row + (int64_t)col * n];
+        }
+        __nv_bfloat16 k1, k2, k3;
+        split3(v, k1, k2, k3);
+        __nv_bfloat16* b = Bp + ((int64_t)q * n + row) * 6 * n + col;
+        b[0] = k1;
+        b[n] = k2;
+        b[2 * n] = k3;
+        b[3 * n] = k1;
+        b[4 * n] = k2;
+        b[5 * n] = k1;
+    }
+}
+
+bool tc_residual_ok(const st_model* m) { return (m->ns * m->nt) % 4 == 0; }
+
+// B' for the model's reduced operators (rebuilt on every call that uses it)
+st_status residual_prepare(st_model* m) {
+    const int n = m->ns * m->nt, R = (m->Q + 1) * n;
+    ST_TRY(st_grow(m, m->mlp.kall16, sizeof(__nv_bfloat16) * (size_t)R * 6 * n + 256));
+    kall_split_kernel<<<grid1d(m, (int64_t)R * n), NT, 0, m->stream>>>(m->ns, m->nt, m->Q, m->d_Ahat, m->d_G, m->d_M,
+                                                                      m->d_S, (__nv_bfloat16*)m->mlp.kall16.p);
+    return st_check_launch("kall split");
+}
+
+// C (rows x R, FP32) = X (rows x n, FP64, ld ldx) K_all^T on the tensor cores
+st_status residual_products(st_model* m, int rows, const double* X, int ldx, float* C) {
+    const int n = m->ns * m->nt, R = (m->Q + 1) * n;
+    ST_TRY(st_grow(m, m->mlp.xsplit, sizeof(__nv_bfloat16) * (size_t)rows * 6 * n + 256));
+    __nv_bfloat16* A = (__nv_bfloat16*)m->mlp.xsplit.p;
+    {
+        ST_PROF(m, "residual_split_kernel");
+        split_rows_kernel<<<grid1d(m, (int64_t)rows * n), NT, 0, m->stream>>>(rows, n, X, ldx, A);
+        ST_TRY(st_check_launch("residual split"));
+    }
+    tc::GemmArgs g = epi(m);
+    g.out_f32 = C;
+    g.ldf = R;
+    return st_tc_gemm(m, bn_for(R), rows, R, 6 * n, A, 6 * n, (const __nv_bfloat16*)m->mlp.kall16.p, 6 * n, g);
+}
+
 // per sample: the final residual of its sorted row; 1 and a slot in the
 // fallback list when it is above the gate (or not finite)
 __global__ void refine_verdict_kernel(int n, const int* __restrict__ pos, const double* __restrict__ rel, double gate,
@@ -1047,11 +1151,17 @@ extern "C" st_status st_rom_refine(st_model* m, int32_t n, const double* mu, con
     } else {
         ST_CUDA_TRY(cudaMemsetAsync(uhat, 0, sizeof(double) * (size_t)n * nf, st));
     }
-    // 2. the affine pieces of Ahat^st
-    ST_TRY(st_grow(m, s.kall, sizeof(float) * (size_t)R * nf));
-    kall_kernel<<<grid1d(m, (int64_t)R * nf), NT, 0, st>>>(m->ns, m->nt, Q, m->d_Ahat, m->d_G, m->d_M, m->d_S,
-                                                           (float*)s.kall.p);
-    ST_TRY(st_check_launch("refine kall"));
+    // 2. the affine pieces of Ahat^st (three-part BF16 splits for the
+    //    tensor-core products, or FP32 for the SIMT ones)
+    const bool tc = tc_residual_ok(m);
+    if (tc) {
+        ST_TRY(residual_prepare(m));
+    } else {
+        ST_TRY(st_grow(m, s.kall, sizeof(float) * (size_t)R * nf));
+        kall_kernel<<<grid1d(m, (int64_t)R * nf), NT, 0, st>>>(m->ns, m->nt, Q, m->d_Ahat, m->d_G, m->d_M, m->d_S,
+                                                               (float*)s.kall.p);
+        ST_TRY(st_check_launch("refine kall"));
+    }
     // 3. samples sorted by nearest reference, each reference's rows padded to
     //    whole tiles
     const int nr = P.n_ref;
@@ -1106,7 +1216,9 @@ extern "C" st_status st_rom_refine(st_model* m, int32_t n, const double* mu, con
     // 4. residual, then correction, until every row meets the gate
     int it = 0;
     for (;; ++it) {
-        {
+        if (tc) {
+            ST_TRY(residual_products(m, rows, Xs, nf, C));
+        } else {
             ST_PROF(m, "gate_gemm_kernel");
             gate_gemm_kernel<<<dim3((R + 63) / 64, (rows + 63) / 64), 256, 0, st>>>(rows, R, nf, Xs, nf,
                                                                                    (float*)s.kall.p, C);

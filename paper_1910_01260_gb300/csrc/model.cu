@@ -268,7 +268,7 @@ void st_model_destroy(st_model* m) {
     for (DevBuf* b : {&m->W, &m->V, &m->ws_fom, &m->ws_pod, &m->ws_pod2, &m->ws_gemm, &m->ws_oz,
                       &m->ws_solve, &m->ws_misc, &m->ws_srom, &m->ws_cert, &m->prec.inv, &m->prec.work, &m->mlp.params, &m->mlp.grad, &m->mlp.adam_m,
                       &m->mlp.adam_v, &m->mlp.wbf, &m->mlp.stats, &m->mlp.act, &m->mlp.kall,
-                      &m->mlp.list})
+                      &m->mlp.list, &m->mlp.kall16, &m->mlp.xsplit})
         cudaFree(b->p);
     for (OzSlot& sl : m->oz_slot) {
         cudaFree(sl.planes.p);

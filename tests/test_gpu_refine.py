@@ -57,8 +57,10 @@ def test_refinement_meets_the_gate_on_the_oracle_residual(c1_setup):
     for k in range(0, 300, 7):
         A, f = rm.operator(p.theta(mu[k]))
         r_oracle = np.linalg.norm(f - A @ U[k]) / np.linalg.norm(f)
-        assert r_oracle <= gate * (1 + 1e-2) + 2e-7            # FP32 products in the library's residual
-        assert abs(r_oracle - rel[k]) <= 2e-7 + 1e-2 * r_oracle
+        # the library's residual uses FP32-accurate products (tensor-core FP32
+        # sums of three-part BF16 splits): a few 1e-7 of ||rhs|| here
+        assert r_oracle <= gate * (1 + 1e-2) + 5e-7
+        assert abs(r_oracle - rel[k]) <= 5e-7 + 1e-2 * r_oracle
         want = np.linalg.solve(A, f)
         assert np.linalg.norm(U[k] - want) / np.linalg.norm(want) <= 100 * gate
     m.close()

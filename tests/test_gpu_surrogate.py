@@ -122,7 +122,9 @@ def test_gate_residual_and_fallback(c1):
     assert np.array_equal(us[clear], (gates[clear] > gate).astype(np.int32))
     for k in range(n):
         if us[k] == 0:
-            assert abs(rr[k] - gates[k]) < 1e-5 * gates[k]
+            # the gate's products are FP32-accurate (tensor-core FP32 sums of
+            # three-part BF16 splits): ~2^-23 of ||Ahat^st x|| ~ ||rhs|| here
+            assert abs(rr[k] - gates[k]) < 1e-5 * gates[k] + 4e-7
             assert rel_max(uh[k], pred) < 1e-6
         else:
             want = rm.solve(th[k])
