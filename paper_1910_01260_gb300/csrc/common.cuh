@@ -58,6 +58,10 @@ __device__ __forceinline__ void red_release_gpu(unsigned int* p, unsigned int v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier of a cooperative launch (every CTA co-resident).  The
 // CTA's writes are ordered before its arrival by the block barrier and the
 // release of the arrival atomic; the last CTA to arrive resets the counter
@@ -94,6 +98,22 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b, int* s_flag) {
     }
     __syncthreads();
     return *s_flag != 0;
+}
+
+// Point-to-point wait of a cooperative launch: one thread spins (acquire)
+// until the counter *f reaches target, bounded like grid_sync; the caller
+// follows with a block barrier.  False after an abort or a timeout.
+__device__ __forceinline__ bool wait_ready(const GridBarrier& b, const unsigned int* f, unsigned int target) {
+    long long it = 0;
+    while (ld_acquire_gpu(f) < target) {
+        if (++it > b.limit) {
+            grid_abort(b, ST_ERR_TIMEOUT);
+            return false;
+        }
+        if (*(volatile unsigned int*)b.abort) return false;
+        __nanosleep(32);
+    }
+    return true;
 }
 
 __device__ __forceinline__ bool st_finite(double x) { return isfinite(x); }

@@ -561,10 +561,13 @@ __global__ void __launch_bounds__(64) larft_kernel(int b, const double* __restri
 // rotates every cross pair (block I column against block J column) in KB
 // inner rounds of KB disjoint pairs, one pair per JW / KB warps; in a sweep's
 // first round the pairs inside each block are rotated as well.  Every pair of
-// columns is thus met once per sweep, as in the classical cyclic ordering,
-// with one grid barrier per block round instead of one per column round.
-// Squared column norms are carried with the rotations and recomputed at the
-// start of every sweep.  The sweep loop stops after a sweep without rotation.
+// columns is thus met once per sweep, as in the classical cyclic ordering.
+// A block pair waits only for its own two blocks: a counter per block holds
+// the round it is ready for, released by the CTA that last rotated it, and
+// grid barriers remain only around the norms and ordering at the start of a
+// sweep and its convergence test at the end.  Squared column norms are
+// carried with the rotations and recomputed at the start of every sweep.
+// The sweep loop stops after a sweep without rotation.
 struct JacArgs {
     int m, n;
     double* X;
@@ -579,17 +582,40 @@ struct JacArgs {
     double* nsort; // [n] the norms at the start of the sweep, for the ordering
     double cut;    // relative singular-value cut below which columns are dropped
     unsigned long long* rotations;  // out: rotations applied (accumulated)
+    unsigned int* ready;  // [ceil(n / KB)] zeroed: the round each column block is ready for
     GridBarrier bar;
 };
 
+// The Jacobi rotation of a column pair with squared norms alpha, beta and
+// product gamma (gamma != 0): the angle with tan 2theta = 2 gamma / (beta -
+// alpha), |theta| <= pi/4.  With d = beta - alpha, h = 2 gamma and r =
+// sqrt(d^2 + h^2), cos 2theta = |d| / r; with w = r + |d| and q = 1 / sqrt(2 r w)
+// this gives c = w q and s = sign(d) h q, and c^2 + s^2 = (w^2 + h^2) q^2 = 1
+// (w^2 + h^2 = 2 r w).  d and h are first scaled by a power of two (exactly)
+// so that the larger lies in [1, 4): no overflow or underflow in d^2 + h^2.
+// One square root and one reciprocal square root: on this GPU's FP64 pipe a
+// dependent square root or division costs about as much as ten FMAs.
 __device__ __forceinline__ void jacobi_pair_rot(double alpha, double beta, double gamma, double& c,
                                                 double& s) {
-    const double zeta = (beta - alpha) / (2.0 * gamma);
-    double t;
-    if (fabs(zeta) > 1e150) t = 0.5 / zeta;
-    else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    c = 1.0 / sqrt(1.0 + t * t);
-    s = c * t;
+    double d = beta - alpha, h = 2.0 * gamma;
+    const long long ex = (__double_as_longlong(fmax(fabs(d), fabs(h))) >> 52) & 0x7ff;
+    const long long ec = ex < 1 ? 1 : (ex > 2045 ? 2045 : ex);
+    const double sc = __longlong_as_double((2046 - ec) << 52);  // 2^(1023 - ec)
+    d *= sc;
+    h *= sc;
+    const double r = sqrt(fma(d, d, h * h));
+    const double w = r + fabs(d);
+    const double q = rsqrt(2.0 * r * w);
+    c = w * q;
+    s = (d < 0.0 ? -h : h) * q;
+}
+
+// Whether a pair is rotated: |gamma| > tol sqrt(alpha beta), squared where
+// alpha beta is finite (no square roots).
+__device__ __forceinline__ bool jacobi_rotates(double alpha, double beta, double gamma, double tol) {
+    const double p = alpha * beta;
+    if (p <= 1.0e308) return gamma * gamma > (tol * tol) * p;
+    return fabs(gamma) > tol * sqrt(alpha) * sqrt(beta);
 }
 
 constexpr int JW = 8;  // warps per Jacobi CTA
@@ -618,10 +644,12 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
     double* sY = sX + (size_t)NC * a.m;         // NC x n
     double* snrm = sY + (size_t)NC * a.n;       // [n] norms, for the ordering
     int* sperm = reinterpret_cast<int*>(snrm + a.n);  // [n] positions -> columns
-    __shared__ double s_part[JW];
+    __shared__ double s_dot[32 * JW];  // per-thread partial dot products
     __shared__ double s_nrm[NC];
     __shared__ int s_dirty[NC];
     __shared__ int s_col[NC];
+    __shared__ int s_rot[KB];
+    __shared__ double s_cs[2 * KB];  // (c, s) of each pair slot
     __shared__ int s_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthr = 32 * JW;
@@ -671,9 +699,20 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
         // after the SVD whatever their rotation, so they are not rotated
         const double cut2 = a.cut * a.cut * __ldcg(a.nrm2 + a.n);
         for (int t = 0; t < nbp - 1; ++t) {
+            // round index over the whole launch: block b is ready for this
+            // round once ready[b] reaches it (every block plays every round)
+            const unsigned int R = (unsigned int)(sweep * (nbp - 1) + t);
             for (int q = blockIdx.x; q < npairs; q += gridDim.x) {
                 int I, J;
                 rr_pair(nbp, t, q, I, J);
+                if (tid == 0) {
+                    int ok = 1;
+                    if (I < nb) ok = wait_ready(a.bar, a.ready + I, R);
+                    if (ok && J < nb) ok = wait_ready(a.bar, a.ready + J, R);
+                    s_flag = ok;
+                }
+                __syncthreads();
+                if (!s_flag) return;
                 int cols[NC];
                 unsigned int vmask = 0;  // bit c: staged column c exists
 #pragma unroll
@@ -726,18 +765,41 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
                         }
                         if (r < a.m) g = fma(xi[r], xj[r], g);
                     }
-                    g = warp_sum(g + g2);
-                    if (lane == 0) s_part[warp] = g;
+                    s_dot[tid] = g + g2;
                     __syncthreads();
-                    double ga = 0.0;
+                    // the first warp of each pair sums the pair's partials and
+                    // one of its threads computes the rotation (the square
+                    // roots cost as much per warp instruction as the pair's
+                    // whole dot product and update)
+                    if (sub == 0) {
+                        double ga = s_dot[pr * WPP * 32 + lane];
 #pragma unroll
-                    for (int w = 0; w < WPP; ++w) ga += s_part[pr * WPP + w];
-                    const double al = s_nrm[i], be = s_nrm[j];
-                    const bool rot = valid && (al > cut2 || be > cut2) &&
-                                     fabs(ga) > a.tol * sqrt(al) * sqrt(be);
-                    double c = 1.0, sn = 0.0;
-                    if (rot) {
-                        jacobi_pair_rot(al, be, ga, c, sn);
+                        for (int w = 1; w < WPP; ++w) ga += s_dot[(pr * WPP + w) * 32 + lane];
+                        ga = warp_sum(ga);
+                        if (lane == 0) {
+                            const double al = s_nrm[i], be = s_nrm[j];
+                            const bool rot = valid && ga != 0.0 && (al > cut2 || be > cut2) &&
+                                             jacobi_rotates(al, be, ga, a.tol);
+                            double c = 1.0, sn = 0.0;
+                            if (rot) {
+                                jacobi_pair_rot(al, be, ga, c, sn);
+                                // new squared norms: c^2 al - 2cs ga + s^2 be and s^2 al + 2cs ga + c^2 be
+                                // (the pairs of a round are disjoint: no other thread reads them now)
+                                const double cs2 = 2.0 * c * sn * ga;
+                                s_nrm[i] = fmax(c * c * al - cs2 + sn * sn * be, 0.0);
+                                s_nrm[j] = fmax(sn * sn * al + cs2 + c * c * be, 0.0);
+                                s_dirty[i] = 1;
+                                s_dirty[j] = 1;
+                                ++rot_count;
+                            }
+                            s_rot[pr] = rot ? 1 : 0;
+                            s_cs[2 * pr] = c;
+                            s_cs[2 * pr + 1] = sn;
+                        }
+                    }
+                    __syncthreads();
+                    if (s_rot[pr]) {
+                        const double c = s_cs[2 * pr], sn = s_cs[2 * pr + 1];
                         for (int r = sub * 32 + lane; r < a.m; r += 32 * WPP) {
                             const double u = xi[r], v = xj[r];
                             xi[r] = c * u - sn * v;
@@ -751,19 +813,9 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
                             yj[r] = sn * u + c * v;
                         }
                     }
-                    // every read of s_part and s_nrm of this inner round is done
+                    // the next inner round reads columns that other warps rotated
                     __syncthreads();
-                    if (rot && sub == 0 && lane == 0) {
-                        // new squared norms: c^2 al - 2cs ga + s^2 be and s^2 al + 2cs ga + c^2 be
-                        const double cs2 = 2.0 * c * sn * ga;
-                        s_nrm[i] = fmax(c * c * al - cs2 + sn * sn * be, 0.0);
-                        s_nrm[j] = fmax(sn * sn * al + cs2 + c * c * be, 0.0);
-                        s_dirty[i] = 1;
-                        s_dirty[j] = 1;
-                        ++rot_count;
-                    }
                 }
-                __syncthreads();
                 bool dirty[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) dirty[c] = s_dirty[c] != 0;
@@ -781,11 +833,18 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
                     __stcg(a.nrm2 + s_col[tid], s_nrm[tid]);
                     *(volatile int*)(a.flags + sweep % 3) = 1;
                 }
-                // shared memory is restaged for the next block pair
+                // every store of this pair is made before the blocks are
+                // released to the next round; shared memory is then restaged
                 __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    if (I < nb) st_release_gpu(a.ready + I, R + 1);
+                    if (J < nb) st_release_gpu(a.ready + J, R + 1);
+                }
             }
-            if (!grid_sync(a.bar, &s_flag)) return;
         }
+        // the convergence flag of the sweep and the columns of its last round
+        if (!grid_sync(a.bar, &s_flag)) return;
         if (*(volatile int*)(a.flags + sweep % 3) == 0) {
             converged = true;
             ++sweep;
@@ -918,7 +977,7 @@ __global__ void __launch_bounds__(512) temporal_kernel(int Nt, int nmu, int ns, 
                 al = warp_sum(al);
                 be = warp_sum(be);
                 ga = warp_sum(ga);
-                if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+                if (ga != 0.0 && jacobi_rotates(al, be, ga, tol)) {
                     double c, s;
                     jacobi_pair_rot(al, be, ga, c, s);
                     for (int r = lane; r < Nt; r += 32) {
@@ -1078,7 +1137,7 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
     double* q_beta = partial + szPart + szPan;  // [cap] R diagonal of the pivoted QR
     double* q_tau = q_beta + cap;        // [cap] Householder coefficients
     double* q_scale = q_tau + cap;       // [cap] 1 / (x_k - beta_k)
-    double* q_nrm = q_scale + cap;       // [2 cap] QR trailing norms (double buffered), then the Jacobi sweep-start norms
+    double* q_nrm = q_scale + cap;       // [2 cap] QR trailing norms (double buffered), then the Jacobi sweep-start norms and block counters
     double* d_sig = q_nrm + 2 * cap;     // [cap] current sigma (device copy)
     double* d_sig_sorted = d_sig + cap;  // [cap]
     double* d_sig_tmp = d_sig_sorted + cap;
@@ -1133,12 +1192,15 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
         // the largest squared column norm is accumulated with atomicMax from zero
         ST_CUDA_TRY(cudaMemsetAsync(d_sig_tmp + ncols, 0, sizeof(double), st));
         ST_CUDA_TRY(cudaMemsetAsync(d_rot, 0, sizeof(unsigned long long), st));
+        // the block readiness counters live in the second half of the QR norms
+        unsigned int* d_ready = reinterpret_cast<unsigned int*>(q_nrm + cap);
+        ST_CUDA_TRY(cudaMemsetAsync(d_ready, 0, sizeof(unsigned int) * nb, st));
         // Z = R^T: stop when every pair of columns is orthogonal to
         // sqrt(m) * eps relative (the left singular vectors of the middle
         // matrix are these columns, normalised)
         JacArgs ja{mrows, ncols, Z, cap, Y, cap, m->opt.jacobi_sweeps,
                    std::sqrt((double)mrows) * 2.220446049250313e-16, d_int + 3, d_int + 2, d_sig_tmp,
-                   q_nrm, 0.1 * m->opt.eps_sv, d_rot, bar};
+                   q_nrm, 0.1 * m->opt.eps_sv, d_rot, d_ready, bar};
         void* args[] = {&ja};
         ST_PROF(m, "jacobi_kernel");
         ST_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(jb), dim3(32 * JW), args, smem, st));
