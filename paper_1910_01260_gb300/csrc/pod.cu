@@ -34,7 +34,7 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
-constexpr int kGsPanel = 64;  // columns per Gram-Schmidt panel
+constexpr int kGsPanel = 128;  // columns per Gram-Schmidt panel
 
 // ---------------------------------------------------------------------------
 // tau = eps * max_j ||U[:, j]||: block (j, c) sums column j over row chunk c
@@ -90,8 +90,12 @@ struct Gs2Args {
     int* k_out;
     const double* tau;  // NULL: every column adds a direction
     double* partial;    // [2 x grid x (m + 2)]
+    unsigned long long* work;  // accumulated: multiply-adds per row (the flop count is 2 N times it)
     GridBarrier bar;
 };
+
+// Shared memory of gs2_kernel: the four coefficient vectors.
+inline size_t gs2_smem(int m) { return sizeof(double) * 4 * (size_t)m; }
 
 __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
     extern __shared__ double sm[];
@@ -102,12 +106,16 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
     double* hn = sm + 2 * (size_t)a.m;
     double* h2n = sm + 3 * (size_t)a.m;
     __shared__ double s_w1[NWARP], s_w2[NWARP];
-    __shared__ double s_nu, s_cross;
+    __shared__ double s_nu, s_inv, s_cross;
     __shared__ int s_flag;
     const int G = gridDim.x, b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t R = (a.N + G - 1) / G;
     const int64_t r0 = (int64_t)b * R, r1 = min(a.N, r0 + R);
+    // element i of column j of E, of direction c of J
+    auto e_ld = [&](int j, int64_t i) -> double { return __ldcg(a.E + (int64_t)j * a.N + i); };
+    auto e_st = [&](int j, int64_t i, double v) { __stcg(a.E + (int64_t)j * a.N + i, v); };
+    auto j_ld = [&](int c, int64_t i) -> double { return __ldcg(a.J + (int64_t)c * a.N + i); };
     const double tau = a.tau ? *a.tau : -1.0;
     // Every block owns rows [r0, r1) of E and J: updates are local and only
     // dot products cross blocks.  A reduction writes per-block partials
@@ -117,7 +125,9 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
     // read.  The norm of column j, its product with column j+1 and the
     // first-pass projections of column j+1 share one reduction (the
     // coefficient on a direction accepted from column j is e_j^T e_{j+1} /
-    // ||e_j||): two grid barriers per column.
+    // ||e_j||): two grid barriers per column.  A dependent FP64 add costs tens
+    // of cycles on this GPU, so the sums below are pairwise and the dot
+    // products keep four independent accumulators.
     const int S = a.m + 2;
     int red = 0;
     auto part = [&](int slot) { return a.partial + ((size_t)(red & 1) * G + b) * S + slot; };
@@ -132,59 +142,66 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         }
         __syncthreads();
         if (tid == 0) {
-            double t1 = 0.0, t2 = 0.0;
+            double t1[NWARP], t2[NWARP];
+#pragma unroll
             for (int w = 0; w < NWARP; ++w) {
-                t1 += s_w1[w];
-                t2 += s_w2[w];
+                t1[w] = s_w1[w];
+                t2[w] = s_w2[w];
             }
-            __stcg(part(a.m), t1);
-            __stcg(part(a.m + 1), t2);
+#pragma unroll
+            for (int h = NWARP / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int w = 0; w < h; ++w) {
+                    t1[w] += t1[w + h];
+                    t2[w] += t2[w + h];
+                }
+            __stcg(part(a.m), t1[0]);
+            __stcg(part(a.m + 1), t2[0]);
         }
     };
-    // fixed-order sum over the blocks of one partial slot (lane-strided, then
-    // across the warp); the loads of four blocks are in flight together
+    // fixed-order sum over the blocks of one partial slot (lane-strided,
+    // pairwise, then across the warp); the loads of eight blocks per lane are
+    // in flight together (one round for up to 256 blocks)
     auto sum_slot = [&](int slot) -> double {
         double acc = 0.0;
-        for (int b0 = lane; b0 < G; b0 += 4 * 32) {
-            double v[4];
+        for (int b0 = lane; b0 < G; b0 += 8 * 32) {
+            double v[8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < 8; ++i) {
                 const int bb = b0 + 32 * i;
                 v[i] = bb < G ? __ldcg(part_of(bb, slot)) : 0.0;
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc += v[i];
+            acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
         }
         return warp_sum(acc);
     };
-    // dot product of this block's rows of two columns (lane-strided, then
-    // across the warp), four rows' loads in flight together
-    auto block_dot = [&](const double* x, const double* y) -> double {
-        double acc = 0.0;
+    // dot product of this block's rows of direction c and column j (lane-
+    // strided, four independent accumulators, then across the warp)
+    auto block_dot = [&](int c, int j) -> double {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
         for (int64_t i0 = r0 + lane; i0 < r1; i0 += 4 * 32) {
             double xv[4], yv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t i = i0 + 32 * u;
-                xv[u] = i < r1 ? __ldcg(x + i) : 0.0;
-                yv[u] = i < r1 ? __ldcg(y + i) : 0.0;
+                xv[u] = i < r1 ? j_ld(c, i) : 0.0;
+                yv[u] = i < r1 ? e_ld(j, i) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc = fma(xv[u], yv[u], acc);
+            for (int u = 0; u < 4; ++u) acc[u] = fma(xv[u], yv[u], acc[u]);
         }
-        return warp_sum(acc);
+        return warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
     };
     int k = 0;   // directions found so far
     int kc = 0;  // directions the finishing column was projected on
+    unsigned long long work = 2;  // multiply-adds per row: ||e_0||^2 and e_0^T e_1
     {
         // column 0 has nothing to project: ||e_0||^2 and e_0^T e_1
-        const double* e0 = a.E;
-        const double* e1 = a.m > 1 ? a.E + a.N : nullptr;
         double n2 = 0.0, cr = 0.0;
         for (int64_t i = r0 + tid; i < r1; i += NT) {
-            const double v = __ldcg(e0 + i);
+            const double v = e_ld(0, i);
             n2 = fma(v, v, n2);
-            if (e1) cr = fma(v, __ldcg(e1 + i), cr);
+            if (a.m > 1) cr = fma(v, e_ld(1, i), cr);
         }
         write_pair(n2, cr);
     }
@@ -197,8 +214,12 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
             const double acc = sum_slot(c < kn ? c : a.m + (c - kn));
             if (lane == 0) {
                 if (c < kn) hn[c] = acc;
-                else if (c == kn) s_nu = sqrt(acc);
-                else s_cross = acc;
+                else if (c == kn) {
+                    // ||e_j|| and its inverse from one reciprocal square root
+                    const double iv = acc > 0.0 ? rsqrt(acc) : 0.0;
+                    s_inv = iv;
+                    s_nu = acc > 0.0 ? acc * iv : sqrt(acc);
+                } else s_cross = acc;
             }
         }
         ++red;
@@ -212,28 +233,37 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         // remainder is above the threshold
         if (b == 0)
             for (int c = tid; c < kc; c += NT) a.P[c + (int64_t)j * a.ldp] = hc[c] + h2c[c];
-        const double* ej = a.E + (int64_t)j * a.N;
         if (nu > tau && nu > 0.0) {
-            const double inv = 1.0 / nu;
+            const double inv = s_inv;
             double* jk = a.J + (int64_t)k * a.N;
-            for (int64_t i = r0 + tid; i < r1; i += NT) __stcg(jk + i, __ldcg(ej + i) * inv);
+            for (int64_t i = r0 + tid; i < r1; i += NT) __stcg(jk + i, e_ld(j, i) * inv);
             if (b == 0 && tid == 0) a.P[k + (int64_t)j * a.ldp] = nu;
             if (tid == 0) hn[k] = s_cross * inv;
             ++k;
         }
         __syncthreads();
         if (j + 1 == a.m) break;
+        // both passes' updates and dot products, the next column's first-pass
+        // dot products, the squared norm and the cross term
+        work += 3 * (unsigned long long)k + (j + 2 < a.m ? k : 0) + 2;
         // column j+1: first pass e -= J(:, 0:k) hn, second-pass projections
-        double* e = a.E + (int64_t)(j + 1) * a.N;
         if (k > 0) {
-            for (int64_t i = r0 + tid; i < r1; i += NT) {
-                double v = __ldcg(e + i);
-                for (int c = 0; c < k; ++c) v = fma(-__ldcg(a.J + (int64_t)c * a.N + i), hn[c], v);
-                __stcg(e + i, v);
+            // two rows per pass of the loop: their chains of k FMAs interleave
+            for (int64_t i = r0 + tid; i < r1; i += 2 * NT) {
+                const int64_t i2 = i + NT;
+                const bool two = i2 < r1;
+                double v = e_ld(j + 1, i), v2 = two ? e_ld(j + 1, i2) : 0.0;
+                for (int c = 0; c < k; ++c) {
+                    const double h = hn[c];
+                    v = fma(-j_ld(c, i), h, v);
+                    if (two) v2 = fma(-j_ld(c, i2), h, v2);
+                }
+                e_st(j + 1, i, v);
+                if (two) e_st(j + 1, i2, v2);
             }
             __syncthreads();
             for (int c = warp; c < k; c += NWARP) {
-                const double acc = block_dot(a.J + (int64_t)c * a.N, e);
+                const double acc = block_dot(c, j + 1);
                 if (lane == 0) __stcg(part(c), acc);
             }
             // reduction B: J(:, 0:k)^T e_{j+1} (second pass)
@@ -248,20 +278,31 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         kc = k;
         // second-pass update of e_{j+1} with its squared norm and its product
         // with e_{j+2}, and the first-pass projections of e_{j+2}
-        const double* e2 = j + 2 < a.m ? a.E + (int64_t)(j + 2) * a.N : nullptr;
+        const bool has2 = j + 2 < a.m;
         double n2 = 0.0, cr = 0.0;
-        for (int64_t i = r0 + tid; i < r1; i += NT) {
-            double v = __ldcg(e + i);
+        for (int64_t i = r0 + tid; i < r1; i += 2 * NT) {
+            const int64_t i2 = i + NT;
+            const bool two = i2 < r1;
+            double v = e_ld(j + 1, i), v2 = two ? e_ld(j + 1, i2) : 0.0;
             if (k > 0) {
-                for (int c = 0; c < k; ++c) v = fma(-__ldcg(a.J + (int64_t)c * a.N + i), h2n[c], v);
-                __stcg(e + i, v);
+                for (int c = 0; c < k; ++c) {
+                    const double h = h2n[c];
+                    v = fma(-j_ld(c, i), h, v);
+                    if (two) v2 = fma(-j_ld(c, i2), h, v2);
+                }
+                e_st(j + 1, i, v);
+                if (two) e_st(j + 1, i2, v2);
             }
             n2 = fma(v, v, n2);
-            if (e2) cr = fma(v, __ldcg(e2 + i), cr);
+            if (has2) cr = fma(v, e_ld(j + 2, i), cr);
+            if (two) {
+                n2 = fma(v2, v2, n2);
+                if (has2) cr = fma(v2, e_ld(j + 2, i2), cr);
+            }
         }
-        if (e2)
+        if (has2)
             for (int c = warp; c < k; c += NWARP) {
-                const double acc = block_dot(a.J + (int64_t)c * a.N, e2);
+                const double acc = block_dot(c, j + 2);
                 if (lane == 0) __stcg(part(c), acc);
             }
         write_pair(n2, cr);
@@ -272,7 +313,10 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         h2c = h2n;
         h2n = t;
     }
-    if (b == 0 && tid == 0) *a.k_out = k;
+    if (b == 0 && tid == 0) {
+        *a.k_out = k;
+        if (a.work) atomicAdd(a.work, work);
+    }
 }
 
 // D(0:rows, 0:cols) += S(0:rows, 0:cols) (column major).
@@ -1101,7 +1145,7 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
     int gs_blocks = 0;
     {
         int per_sm = 0;
-        size_t smem = sizeof(double) * 4 * pdim;
+        size_t smem = gs2_smem(pdim);
         if (smem > 48 * 1024)
             ST_CUDA_TRY(cudaFuncSetAttribute(gs2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs2_kernel, NT, smem));
@@ -1146,6 +1190,9 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
     int* d_perm = d_int + 16;            // [cap]
     int* d_piv = d_perm + cap;           // [cap] column pivots of the QR
     unsigned long long* d_rot = reinterpret_cast<unsigned long long*>(d_scalar + 4);
+    // Gram-Schmidt multiply-adds per row, accumulated over the update (profiling)
+    unsigned long long* d_gs_work = reinterpret_cast<unsigned long long*>(d_scalar + 5);
+    ST_CUDA_TRY(cudaMemsetAsync(d_gs_work, 0, sizeof(unsigned long long), st));
     double* W = (double*)m->W.p;
     double* V = (double*)m->V.p;
 
@@ -1250,12 +1297,12 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
             }
             ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
             double* Jn = Jout + (size_t)k * N;
-            Gs2Args g{N, pw, Ep, Jn, Pp + k, ldp, d_int, tau, partial, bar};
+            Gs2Args g{N, pw, Ep, Jn, Pp + k, ldp, d_int, tau, partial, d_gs_work, bar};
             void* args[] = {&g};
             {
                 ST_PROF(m, "gs2_kernel");
                 ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT), args,
-                                                        sizeof(double) * 4 * kGsPanel, st));
+                                                        gs2_smem(pw), st));
                 st_count_launch();
             }
             int kp = 0;
@@ -1443,21 +1490,22 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
                 ++m->pod_reorth;
                 ST_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)r * r, st));
                 ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
-                Gs2Args g{N, r, W, W2, P, r, d_int, nullptr, partial, bar};
+                Gs2Args g{N, r, W, W2, P, r, d_int, nullptr, partial, d_gs_work, bar};
                 void* args[] = {&g};
                 ST_PROF(m, "gs2_kernel");
                 ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT),
-                                                        args, sizeof(double) * 4 * pdim, st));
-        st_count_launch();
+                                                        args, gs2_smem(r), st));
+                st_count_launch();
                 ST_CUDA_TRY(cudaMemcpyAsync(W, W2, sizeof(double) * N * r, cudaMemcpyDeviceToDevice, st));
             }
         }
     }
     h_sig.resize(std::max(r, 1));
-    if (r > 0) {
-        ST_CUDA_TRY(cudaMemcpyAsync(h_sig.data(), d_sig, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
-        ST_CUDA_TRY(cudaStreamSynchronize(st));
-    }
+    unsigned long long gs_work = 0;
+    ST_CUDA_TRY(cudaMemcpyAsync(&gs_work, d_gs_work, sizeof(gs_work), cudaMemcpyDeviceToHost, st));
+    if (r > 0) ST_CUDA_TRY(cudaMemcpyAsync(h_sig.data(), d_sig, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
+    ST_CUDA_TRY(cudaStreamSynchronize(st));
+    st_prof_flops(m, "gs2_kernel", 2.0 * (double)N * (double)gs_work);
     m->pod_r = r;
     m->pod_rows = rows;
     m->sigma.assign(h_sig.begin(), h_sig.begin() + r);
