@@ -165,29 +165,81 @@ __device__ __forceinline__ void spmv_A(const FomArgs& a, int64_t row, int p0, co
     }
 }
 
+// Reduce-scatter of V values per lane over the lanes of a warp that share
+// (lane % LPR): at each of the log2(32 / LPR) shuffle levels (offsets 16, 8,
+// ...) a lane keeps half of its values and adds its partner's copy of them,
+// until one value is left, then plain butterflies follow.  A lane ends with
+// the totals of values [base, base + KEEP) in x[0, KEEP); every lane whose
+// plain-level bits are zero holds a distinct set.  It takes about V + log2(32
+// / LPR) adds per lane instead of V log2(32 / LPR) for separate butterflies
+// (an FP64 add costs a warp-instruction slot of the FP64 pipe).
+template <int V, int LPR>
+struct RsSum {
+    static constexpr int LEVELS = LPR >= 32 ? 0 : (LPR >= 16 ? 1 : LPR >= 8 ? 2 : LPR >= 4 ? 3 : LPR >= 2 ? 4 : 5);
+    static constexpr int LOGV = V >= 4 ? 2 : (V >= 2 ? 1 : 0);
+    static constexpr int H = LOGV < LEVELS ? LOGV : LEVELS;  // halving levels
+    static constexpr int KEEP = V >> H;
+    static constexpr int PLAIN = LEVELS - H;
+    __device__ __forceinline__ static int run(double (&x)[V], int lane) {
+        int base = 0;
+        int o = 16;
+#pragma unroll
+        for (int lev = 0; lev < H; ++lev, o >>= 1) {
+            const int h = V >> (lev + 1);
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const double send = up ? x[i] : x[i + h];
+                const double keep = up ? x[i + h] : x[i];
+                x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+            base += up ? h : 0;
+        }
+#pragma unroll
+        for (int lev = 0; lev < PLAIN; ++lev, o >>= 1)
+#pragma unroll
+            for (int i = 0; i < KEEP; ++i) x[i] += __shfl_xor_sync(0xffffffffu, x[i], o);
+        return base;
+    }
+    // whether this lane writes its totals (its plain-level bits are zero)
+    __device__ __forceinline__ static bool writer(int lane) { return ((lane / LPR) & ((1 << PLAIN) - 1)) == 0; }
+};
+
 // Reduce per-thread contributions (NS slots x VEC samples) to this block's
-// partial sums.
+// partial sums: a reduce-scatter in each warp, then a pairwise sum over the
+// warps.
 template <int LD, int NS>
 __device__ __forceinline__ void block_partial(double (&c)[NS][Cfg<LD>::VEC], double* partial,
                                               double (*s_warp)[NSLOT][LD], int bid) {
     constexpr int VEC = Cfg<LD>::VEC, LPR = Cfg<LD>::LPR, NW = Cfg<LD>::NW;
+    constexpr int V = NS * VEC;
+    using RS = RsSum<V, LPR>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double x[V];
 #pragma unroll
     for (int sl = 0; sl < NS; ++sl)
 #pragma unroll
-        for (int u = 0; u < VEC; ++u) {
-            double x = c[sl][u];
+        for (int u = 0; u < VEC; ++u) x[sl * VEC + u] = c[sl][u];
+    const int base = RS::run(x, lane);
+    if (RS::writer(lane)) {
+        const int lr = lane % LPR;
 #pragma unroll
-            for (int o = LPR; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane < LPR) s_warp[warp][sl][lane * VEC + u] = x;
+        for (int i = 0; i < RS::KEEP; ++i) {
+            const int v = base + i;
+            s_warp[warp][v / VEC][lr * VEC + v % VEC] = x[i];
         }
+    }
     __syncthreads();
     if (threadIdx.x < NS * LD) {
         const int sl = threadIdx.x / LD, p = threadIdx.x % LD;
-        double acc = 0.0;
+        double t[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) acc += s_warp[w][sl][p];
-        __stcg(partial + ((int64_t)bid * NS + sl) * LD + p, acc);
+        for (int w = 0; w < NW; ++w) t[w] = s_warp[w][sl][p];
+#pragma unroll
+        for (int h = NW / 2; h > 0; h >>= 1)
+#pragma unroll
+            for (int w = 0; w < h; ++w) t[w] += t[w + h];
+        __stcg(partial + ((int64_t)bid * NS + sl) * LD + p, t[0]);
     }
 }
 
