@@ -310,7 +310,14 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
     const int rb = threadIdx.x / LPR;
     const int p0 = lr * VEC;
     const int64_t N = a.N;
-    const int64_t nchunks = (N + RPB - 1) / RPB;
+    // this CTA's rows: a contiguous, balanced share of the kSlice-row slices
+    // (so a warp's rows stay in one slice), swept in passes of RPB rows.  A
+    // round-robin deal of RPB-row chunks would give some CTAs a whole pass
+    // more than others (96 chunks over 19 CTAs at N = 49152), and every
+    // phase waits for the slowest CTA at its barrier.
+    const int64_t nsl = (N + kSlice - 1) / kSlice;
+    const int64_t row_lo = (nsl * bid / nblk) * kSlice;
+    const int64_t row_hi = min(N, (nsl * (bid + 1) / nblk) * kSlice);
 
     if (threadIdx.x < LD) {
         s_state[threadIdx.x] = threadIdx.x < a.n_mu ? S_ACTIVE : S_PAD;
@@ -330,9 +337,7 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
 #define PART (a.partial + (size_t)(red & 1) * part_stride)
 
 #define ROWS_BEGIN                                                                    \
-    for (int64_t ch = bid; ch < nchunks; ch += nblk) {                               \
-        const int64_t row = ch * RPB + rb;                                            \
-        if (row >= N) continue;                                                       \
+    for (int64_t row = row_lo + rb; row < row_hi; row += RPB) {                       \
         const int64_t vi = row * LD + p0;
 #define ROWS_END }
 
