@@ -167,6 +167,25 @@ __device__ bool panel_factor(T* P, int rp, int w, int ld_p, int* pp, T (*s_cv)[N
 // L11^{-1} A12 with the explicit inverse of the unit lower 32 x 32 block, and
 // A22 -= L21 U12 in register-tiled column chunks.  Returns false if a zero
 // pivot occurred (the factorisation still completes, as in LAPACK).
+// P (shared, ld ld_p) <- the rp x w block of A at (kb, kb) (global, ld n):
+// warp per column, lane per row, four rows' loads in flight per lane.
+template <typename T>
+__device__ __forceinline__ void panel_load(T* P, int ld_p, const T* A, int n, int kb, int rp, int w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = warp; c < w; c += NWARP) {
+        const T* src = A + kb + (int64_t)(kb + c) * n;
+        T* dst = P + (size_t)c * ld_p;
+        for (int r0 = lane; r0 < rp; r0 += 4 * 32) {
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = r0 + 32 * u < rp ? src[r0 + 32 * u] : (T)0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (r0 + 32 * u < rp) dst[r0 + 32 * u] = v[u];
+        }
+    }
+}
+
 template <typename T>
 __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[NWARP], int (*s_ci)[NWARP],
                           int* s_npl) {
@@ -175,10 +194,7 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[N
     const int cap = ld_p * nb;  // elements of the panel buffer, reused as staging
     for (int kb = 0; kb < n; kb += nb) {
         const int w = min(nb, n - kb), rp = n - kb;
-        for (int t = tid; t < rp * w; t += NT) {
-            const int r = t % rp, c = t / rp;
-            s.P[r + c * ld_p] = A[(kb + r) + (int64_t)(kb + c) * n];
-        }
+        panel_load(s.P, ld_p, A, n, kb, rp, w);
         for (int r = tid; r < rp; r += NT) {
             s.cur[r] = r;
             s.where[r] = r;
@@ -216,10 +232,8 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[N
         }
         __syncthreads();
         // the panel back in its final row order
-        for (int t = tid; t < rp * w; t += NT) {
-            const int r = t % rp, c = t / rp;
-            A[(kb + r) + (int64_t)(kb + c) * n] = s.P[s.cur[r] + c * ld_p];
-        }
+        for (int c = warp; c < w; c += NWARP)
+            for (int r = lane; r < rp; r += 32) A[(kb + r) + (int64_t)(kb + c) * n] = s.P[s.cur[r] + c * ld_p];
         __syncthreads();
         // the moved rows of the columns outside the panel: gather all, then scatter
         const int npl = *s_npl, nout = n - w;
@@ -242,10 +256,7 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[N
             }
         }
         // the factorised panel again, in its final row order
-        for (int t = tid; t < rp * w; t += NT) {
-            const int r = t % rp, c = t / rp;
-            s.P[r + c * ld_p] = A[(kb + r) + (int64_t)(kb + c) * n];
-        }
+        panel_load(s.P, ld_p, A, n, kb, rp, w);
         __syncthreads();
         const int r22 = n - kb - w;
         if (r22 <= 0) continue;
@@ -306,28 +317,32 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[N
                 const int r = t % w, c = t / w;
                 A[(kb + r) + (int64_t)(j0 + c) * n] = s.U[r * CWP + c];
             }
-            // A22 -= L21 U12: thread (rg, cg) owns rows RT rg .. RT rg + RT - 1
-            // and columns 8 cg .. 8 cg + 7 of a (32 RT) x 64 tile; the tile's
-            // old values are loaded first (one round of independent loads)
-            // and updated in registers
+            // A22 -= L21 U12: warp `warp` owns columns 8 warp .. 8 warp + 7 of
+            // a (32 RT) x 64 tile and lane `lane` its rows lane + 32 a (a <
+            // RT), so that every load and store of the tile is one contiguous
+            // 32-row segment of a column per warp; the tile's old values are
+            // loaded first (one round of independent loads) and updated in
+            // registers
             constexpr int RT = sizeof(T) == 4 ? 8 : 4;  // FP64: fewer rows (registers)
-            const int cg = tid % 8, rg = tid / 8;
+            static_assert(NT / 32 * 8 == CW, "eight columns per warp cover the chunk");
+            const int cg = warp;
             for (int rt = 0; rt < r22; rt += 32 * RT) {
-                const int rb = rt + RT * rg;  // first row (of A22) of this thread
-                if (rb < r22 && 8 * cg < wc) {
+                if (8 * cg < wc) {
                     T acc[RT][8];
 #pragma unroll
                     for (int a2 = 0; a2 < RT; ++a2)
 #pragma unroll
                         for (int b2 = 0; b2 < 8; ++b2) {
-                            const int rr = rb + a2, c2 = 8 * cg + b2;
+                            const int rr = rt + lane + 32 * a2, c2 = 8 * cg + b2;
                             acc[a2][b2] = (rr < r22 && c2 < wc) ? A[(kb + w + rr) + (int64_t)(j0 + c2) * n] : (T)0;
                         }
                     for (int cc = 0; cc < w; ++cc) {
                         T lv[RT], uv[8];
 #pragma unroll
-                        for (int a2 = 0; a2 < RT; ++a2)
-                            lv[a2] = rb + a2 < r22 ? s.P[(w + rb + a2) + cc * ld_p] : (T)0;
+                        for (int a2 = 0; a2 < RT; ++a2) {
+                            const int rr = rt + lane + 32 * a2;
+                            lv[a2] = rr < r22 ? s.P[(w + rr) + cc * ld_p] : (T)0;
+                        }
 #pragma unroll
                         for (int b2 = 0; b2 < 8; ++b2) uv[b2] = s.U[cc * CWP + 8 * cg + b2];
 #pragma unroll
@@ -339,7 +354,7 @@ __device__ bool lu_factor(T* A, int n, int ld_p, int nb, Smem<T>& s, T (*s_cv)[N
                     for (int a2 = 0; a2 < RT; ++a2)
 #pragma unroll
                         for (int b2 = 0; b2 < 8; ++b2) {
-                            const int rr = rb + a2, c2 = 8 * cg + b2;
+                            const int rr = rt + lane + 32 * a2, c2 = 8 * cg + b2;
                             if (rr < r22 && c2 < wc) A[(kb + w + rr) + (int64_t)(j0 + c2) * n] = acc[a2][b2];
                         }
                 }
@@ -531,25 +546,45 @@ __global__ void __launch_bounds__(NT, 2) solve_kernel(SolveArgs g) {
         if (g.fp32_asm)
             for (int t = tid; t < a * a; t += NT) ah32[t] = (float)s.Ah[t];
         __syncthreads();
-        // assemble Ahat^st (FP64, or FP32 products in the FP32-assembly mode)
-        for (int64_t t = tid; t < (int64_t)n * n; t += NT) {
-            const int row = (int)(t % n), col = (int)(t / n);
-            T v;
-            if (g.fp32_asm) {
-                const int rc = s.perm[row], cc = s.perm[col];
-                const int ip = rc & 0xffff, jp = rc >> 16, i = cc & 0xffff, j = cc >> 16;
-                const int64_t gi = (int64_t)(ip + g.ns * jp) + (int64_t)(i + g.ns * j) * nfull;
-                float f = -ah32[ip + i * a] * g.G32[gi];
-                if (ip == i) {
-                    const int64_t mi = (int64_t)i * g.nt * g.nt + jp + (int64_t)j * g.nt;
-                    f += (float)(g.M[mi] - g.S[mi]);
+        // assemble Ahat^st (FP64, or FP32 products in the FP32-assembly mode):
+        // warp w builds columns w, w + NWARP, ..., lane l rows l, l + 32, ...,
+        // four rows' operand loads in flight per lane
+        {
+            const int lane = tid & 31, warp = tid >> 5;
+            for (int col = warp; col < n; col += NWARP) {
+                const int cc = s.perm[col], i = cc & 0xffff, j = cc >> 16;
+                T* Ac = A + (int64_t)col * n;
+                if (g.fp32_asm) {
+                    const float* Gc = g.G32 + (int64_t)(i + g.ns * j) * nfull;
+                    for (int r0 = lane; r0 < n; r0 += 4 * 32) {
+                        float gv[4];
+                        int rc[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int row = r0 + 32 * u;
+                            rc[u] = row < n ? s.perm[row] : 0;
+                            gv[u] = row < n ? Gc[(rc[u] & 0xffff) + g.ns * (rc[u] >> 16)] : 0.0f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int row = r0 + 32 * u;
+                            if (row >= n) break;
+                            const int ip = rc[u] & 0xffff, jp = rc[u] >> 16;
+                            float f = -ah32[ip + i * a] * gv[u];
+                            if (ip == i) {
+                                const int64_t mi = (int64_t)i * g.nt * g.nt + jp + (int64_t)j * g.nt;
+                                f += (float)(g.M[mi] - g.S[mi]);
+                            }
+                            Ac[row] = (T)f;
+                        }
+                    }
+                } else {
+                    for (int row = lane; row < n; row += 32) {
+                        const int rc = s.perm[row];
+                        Ac[row] = (T)st_entry(g, s.Ah, a, rc & 0xffff, rc >> 16, i, j);
+                    }
                 }
-                v = (T)f;
-            } else {
-                const int rc = s.perm[row], cc = s.perm[col];
-                v = (T)st_entry(g, s.Ah, a, rc & 0xffff, rc >> 16, cc & 0xffff, cc >> 16);
             }
-            A[row + (int64_t)col * n] = v;
         }
         __syncthreads();
         const bool ok = lu_factor(A, n, nfull, nb, s, s_cv, s_ci, &s_npl);
