@@ -144,13 +144,27 @@ __device__ bool panel_factor(T* P, int rp, int w, int ld_p, int* pp, T (*s_cv)[N
         if (pv == (T)0) ok = false;
         const T inv = pv != (T)0 ? (T)1 / pv : (T)1;  // a zero pivot column is all zero: nothing to scale
         if (pr % NT == tid) used |= 1u << (pr / NT);
+        // the row updates in chunks of eight columns, each chunk's loads (pivot
+        // row and own row) before its stores, so that a store can hold up at
+        // most the next chunk's loads (the compiler cannot tell the rows apart)
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
             const int r = tid + k * NT;
             if (r < rp && !((used >> k) & 1u)) {
                 const T l = P[r + c * ld_p] * inv;
                 P[r + c * ld_p] = l;
-                for (int cc = c + 1; cc < w; ++cc) P[r + cc * ld_p] = fma(-l, P[pr + cc * ld_p], P[r + cc * ld_p]);
+                for (int c0 = c + 1; c0 < w; c0 += 8) {
+                    T pv8[8], rv8[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const bool in = c0 + u < w;
+                        pv8[u] = in ? P[pr + (c0 + u) * ld_p] : (T)0;
+                        rv8[u] = in ? P[r + (c0 + u) * ld_p] : (T)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (c0 + u < w) P[r + (c0 + u) * ld_p] = fma(-l, pv8[u], rv8[u]);
+                }
             }
         }
         if (c + 1 < w) scan(c + 1, buf ^ 1);
