@@ -1,7 +1,8 @@
 // Reconstruction u^st ~= Phi_st uhat by blocks (Eqs. blockstructure,
 // ststateapproximation): each spatial mode i has its own temporal basis, so
 //   C_p[i, k] = sum_{j < nt_p} uhat_p[i + ns_p j] phi_t^{i,j}[k]   (i < ns_p, else 0)
-//   u_p^k     = Phi_s C_p[:, k]             (FP64 GEMM, batched over samples)
+//   u_p^k     = Phi_s C_p[:, k]             (one FP64 GEMM for all samples:
+//               the C_p lie side by side, and so do the u_p)
 //   y_p^k     = Chat^T C_p[:, k], Chat = Phi_s^T Cout   (outputs, Eq.
 //               outputFromReducedsol, without forming u)
 #include <algorithm>
@@ -36,6 +37,25 @@ __global__ void temporal_contract_kernel(int n_mu, int ns, int nt, int Nt,
     }
 }
 
+// y[o, c] = sum_i Chat[i, o] C[i, c] for the ncols columns of all samples'
+// C side by side (ns x ncols, ld ns): one output per thread, the ns products
+// in order.  n_out is a handful of functionals, far too few rows for a GEMM
+// tile.
+__global__ void outputs_kernel(int ns, int n_out, int64_t ncols, const double* __restrict__ Chat,
+                               const double* __restrict__ C, double* y) {
+    const int64_t tot = ncols * n_out;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(t % n_out);
+        const int64_t c = t / n_out;
+        const double* cc = C + c * ns;
+        const double* ch = Chat + (int64_t)o * ns;
+        double v = 0.0;
+        for (int i = 0; i < ns; ++i) v = fma(ch[i], cc[i], v);
+        y[t] = v;  // y_p is n_out x Nt: column c of all samples at o + n_out c
+    }
+}
+
 }  // namespace
 
 extern "C" st_status st_rom_reconstruct(st_model* m, int32_t n_mu, const double* uhat,
@@ -61,20 +81,17 @@ extern "C" st_status st_rom_reconstruct(st_model* m, int32_t n_mu, const double*
         temporal_contract_kernel<<<gb, 256, 0, st>>>(n_mu, ns, nt, Nt, uhat, ns_nt, m->d_T, C);
         ST_TRY(st_check_launch("temporal_contract"));
     }
-    const int64_t sCp = (int64_t)ns * Nt;
-    for (int p0 = 0; p0 < n_mu; p0 += 65535) {
-        const int nb = std::min(65535, n_mu - p0);
-        if (u)
-            ST_TRY(st_dgemm(m, false, false, N, Nt, ns, 1.0, m->d_phi, N, C + p0 * sCp, ns, 0.0,
-                            u + (size_t)p0 * N * Nt, N, nb, 0, sCp, N * (int64_t)Nt));
-    }
+    // u = Phi_s [C_0 ... C_{n_mu-1}]: N x (Nt n_mu), sample p's field at
+    // column p Nt (one product, on the tensor cores when it is large)
+    if (u)
+        ST_TRY(st_dgemm(m, false, false, N, (int64_t)Nt * n_mu, ns, 1.0, m->d_phi, N, C, ns, 0.0, u, N));
     if (y) {
         ST_TRY(st_dgemm(m, true, false, ns, n_out, N, 1.0, m->d_phi, N, Cout, N, 0.0, Chat, ns));
-        for (int p0 = 0; p0 < n_mu; p0 += 65535) {
-            const int nb = std::min(65535, n_mu - p0);
-            ST_TRY(st_dgemm(m, true, false, n_out, Nt, ns, 1.0, Chat, ns, C + p0 * sCp, ns, 0.0,
-                            y + (size_t)p0 * n_out * Nt, n_out, nb, 0, sCp, (int64_t)n_out * Nt));
-        }
+        const int64_t ncols = (int64_t)Nt * n_mu;
+        const int gy = (int)std::max<int64_t>(1, std::min<int64_t>((ncols * n_out + 255) / 256, 8 * m->num_sms));
+        ST_PROF(m, "outputs_kernel");
+        outputs_kernel<<<gy, 256, 0, st>>>(ns, n_out, ncols, Chat, C, y);
+        ST_TRY(st_check_launch("outputs"));
     }
     return ST_OK;
 }
