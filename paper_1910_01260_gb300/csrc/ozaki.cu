@@ -99,19 +99,21 @@ __global__ void __launch_bounds__(256) exp_kernel(int64_t R, int64_t K, const do
     if (tid < kTile && r0 + tid < R && s_max[tid] > 0) atomicMax(&emax[r0 + tid], s_max[tid]);
 }
 
-// BF16 bit pattern of an integer with |v| <= 128 (exact).
-__device__ __forceinline__ uint32_t bf16_of_int(int v) {
-    if (v == 0) return 0u;
-    const uint32_t a = (uint32_t)(v < 0 ? -v : v);
-    const int e = 31 - __clz(a);  // 0..7
-    const uint32_t man = (a << (7 - e)) & 0x7Fu;
-    return (v < 0 ? 0x8000u : 0u) | ((uint32_t)(127 + e) << 7) | man;
-}
-
 // Balanced base-128 digits of |x| 2^(56 - e) (e = emax - 1021: the row
 // scale), sign on every digit, packed as BF16 into plane t of `packed` at
 // half-word h.
+//
+// The scaled magnitude X < 2^55 is cut into three 21-bit chunks (bits 0-20,
+// 21-41, 42-54), each an exact FP32 value (2^23 + c - 2^23), so that the
+// digits come from FP32 operations, all exact: q = rint(f / 128) (by the
+// rounding constant 1.5 * 2^23; |f| / 128 < 2^15), r = f - 128 q with
+// |r| <= 64, and the quotient carried into the next chunk.  A chunk holds
+// three digits; the last quotient is the leading digit (X < 2^55: |d_0| <=
+// 64).  A digit is an integer of at most seven bits, so its BF16 pattern is
+// the upper half of its FP32 pattern.  (The integer pipe, which bit-by-bit
+// digit and BF16 arithmetic would load, is half as wide as the FP32 one.)
 __device__ __forceinline__ void put_digits(double x, int emax, uint32_t (&packed)[kSlices][4], int h) {
+    static_assert(kSlices == 8, "three 21-bit chunks of three, three and two digits");
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int E = (int)((b >> 52) & 0x7FF);
     unsigned long long X = 0;
@@ -120,21 +122,34 @@ __device__ __forceinline__ void put_digits(double x, int emax, uint32_t (&packed
         const int s = E - emax + 2;  // <= 2: X < 2^55
         X = s >= 0 ? mant << s : (s > -64 ? mant >> (-s) : 0ull);
     }
-    const bool neg = (b >> 63) != 0;
-    int d[kSlices];
+    const uint32_t lo = (uint32_t)X, hi = (uint32_t)(X >> 32);
+    const float sg = (b >> 63) ? -1.0f : 1.0f;
+    constexpr float kTwo23 = 8388608.0f, kRound = 12582912.0f;
+    float f0 = sg * (__uint_as_float(0x4B000000u | (lo & 0x1FFFFFu)) - kTwo23);
+    float f1 = sg * (__uint_as_float(0x4B000000u | (((lo >> 21) | (hi << 11)) & 0x1FFFFFu)) - kTwo23);
+    float f2 = sg * (__uint_as_float(0x4B000000u | (hi >> 10)) - kTwo23);
+    float d[kSlices];
+    auto step = [&](float& f) -> float {
+        const float q = __fadd_rn(__fmul_rn(f, 0.0078125f), kRound) - kRound;
+        const float r = __fmaf_rn(-128.0f, q, f);
+        f = q;
+        return r;
+    };
+    d[7] = step(f0);
+    d[6] = step(f0);
+    d[5] = step(f0);
+    f1 += f0;
+    d[4] = step(f1);
+    d[3] = step(f1);
+    d[2] = step(f1);
+    f2 += f1;
+    d[1] = step(f2);
+    d[0] = f2;
 #pragma unroll
-    for (int t = kSlices - 1; t >= 1; --t) {
-        int r = (int)(X & 127ull);
-        X >>= 7;
-        if (r >= 64) {
-            r -= 128;
-            X += 1;
-        }
-        d[t] = r;
+    for (int t = 0; t < kSlices; ++t) {
+        const uint32_t bits = __float_as_uint(d[t]);
+        packed[t][h >> 1] |= (h & 1) ? (bits & 0xFFFF0000u) : (bits >> 16);
     }
-    d[0] = (int)X;  // X < 2^55 before the carries: d_0 <= 64
-#pragma unroll
-    for (int t = 0; t < kSlices; ++t) packed[t][h >> 1] |= bf16_of_int(neg ? -d[t] : d[t]) << (16 * (h & 1));
 }
 
 // Digit planes: plane t holds digit t of every element, row-major R x Kp
