@@ -207,6 +207,7 @@ struct OzArgs {
     double* part;  // [chunks][M x N] partial products, or null (single chunk)
     int32_t* err;
     long long limit;
+    int n_fast;  // grid x runs over the N tiles (y over the M tiles), else the reverse
 };
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -262,7 +263,8 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const __grid_const
     const uint32_t a_full = tc::smem_u32(&bars[0]), a_empty = tc::smem_u32(&bars[kARing]);
     const uint32_t b_full = tc::smem_u32(&bars[2 * kARing]), b_empty = tc::smem_u32(&bars[2 * kARing + 2]);
     const uint32_t done = tc::smem_u32(&bars[2 * kARing + 4]);
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN, chunk = blockIdx.z;
+    const int m0 = (g.n_fast ? blockIdx.y : blockIdx.x) * kBM, n0 = (g.n_fast ? blockIdx.x : blockIdx.y) * kBN;
+    const int chunk = blockIdx.z;
     const int kbeg = chunk * g.chunk;
     const int klen = min(g.chunk, g.K - kbeg);
     const int nks = (klen + kBK - 1) / kBK;
@@ -528,7 +530,13 @@ st_status st_ozaki_gemm(st_model* m, bool transA, bool transB, int64_t M, int64_
     CUtensorMap ta, tb;
     ST_TRY(st_tmap_bf16_3d(&ta, planesA, Kp, M, kSlices, Kp, M * Kp, kBK, kBM, 1));
     ST_TRY(st_tmap_bf16_3d(&tb, planesB, Kp, Nc, kSlices, Kp, Nc * Kp, kBK, kBN, kSlices));
-    OzArgs g{(int)M, (int)Nc, (int)K, (int)chunk, ea, eb, alpha, beta, C, ldc, part, m->d_err, m->opt.spin_limit};
+    // tile order: with more M tiles than N tiles the N tiles run fastest, so
+    // that the CTAs of a wave share the digit planes of a few M tiles (a tall
+    // product would otherwise stream all of op(A)'s planes once per N tile)
+    const int64_t mt = (M + kBM - 1) / kBM, nt = (Nc + kBN - 1) / kBN;
+    const int n_fast = mt > nt ? 1 : 0;
+    OzArgs g{(int)M, (int)Nc, (int)K, (int)chunk, ea, eb, alpha, beta, C, ldc, part, m->d_err, m->opt.spin_limit,
+             n_fast};
     {
         ST_PROF(m, "ozaki_gemm_kernel");
         st_prof_flops(m, "ozaki_gemm_kernel", 2.0 * (double)M * (double)Nc * (double)K);
@@ -537,7 +545,7 @@ st_status st_ozaki_gemm(st_model* m, bool transA, bool transB, int64_t M, int64_
             ST_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
             attr = true;
         }
-        const dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((Nc + kBN - 1) / kBN), (unsigned)chunks);
+        const dim3 grid((unsigned)(n_fast ? nt : mt), (unsigned)(n_fast ? mt : nt), (unsigned)chunks);
         oz_gemm_kernel<<<grid, kThreads, kSmem, st>>>(ta, tb, g);
         ST_TRY(st_check_launch("ozaki gemm"));
     }
