@@ -975,7 +975,10 @@ def run_case(case: str) -> None:
     mlp: surrogate forward (tcgen05 GEMMs) on 65,536 parameters;
     fomfull: the full 200-step march of the 16 training parameters, timed;
     podstream: full-size snapshots, the POD by blocks of 8 samples and by the
-    rank-one stream (one snapshot per update, 3200 updates), timed."""
+    rank-one stream (one snapshot per update, 3200 updates), timed;
+    gemm: the FP64-accurate tensor-core GEMM (st_gemm_f64) on the POD's four
+    product shapes with seeded operands, timed, with its error against an FP64
+    reference product."""
     import torch
 
     import paper_1910_01260_gb300 as st
@@ -987,6 +990,40 @@ def run_case(case: str) -> None:
                  stream=stream.cuda_stream)
     B = torch.tensor(prob.B.T.copy(), device=dev)
     n_train = len(prob.train_mu)
+    if case == "gemm":
+        # the POD's products at c4: the W projection of a block of 8 samples
+        # (W^T U, then U - W L) and a Gram-Schmidt panel's (J^T E, E - J P)
+        g = torch.Generator(device="cpu").manual_seed(1)
+        N = prob.N
+        out = {}
+        for name, ta, M, Nc, K in (("W^T U", True, 200, 1600, N), ("U - W L", False, N, 1600, 200),
+                                   ("J^T E", True, 250, 128, N), ("E - J P", False, N, 128, 250)):
+            # column-major operands as row-major tensors of their transposes
+            A = torch.randn((M, K) if ta else (K, M), generator=g, dtype=torch.float64).to(dev)
+            Bm = torch.randn(Nc, K, generator=g, dtype=torch.float64).to(dev)
+            C = torch.zeros(Nc, M, dtype=torch.float64, device=dev)
+            lda = K if ta else M
+            for _ in range(2):
+                m.st_gemm_f64(ta, False, M, Nc, K, 1.0, A, lda, Bm, K, 0.0, C, M)
+            m.st_sync()
+            m.st_profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record(stream)
+            for _ in range(reps):
+                m.st_gemm_f64(ta, False, M, Nc, K, 1.0, A, lda, Bm, K, 0.0, C, M)
+            e1.record(stream)
+            m.st_sync()
+            torch.cuda.synchronize()
+            prof = m.st_profile_read()
+            m.st_profile_enable(False)
+            ms = e0.elapsed_time(e1) / reps
+            ref = (A if ta else A.T) @ Bm.T
+            err = float(((C.T - ref).abs().max() / ref.abs().max()).item())
+            out[name] = {"M": M, "N": Nc, "K": K, "ms": ms, "tflops_fp64_equivalent": 2.0 * M * Nc * K / ms / 1e9,
+                         "max_rel_err": err, "kernels_ms": {k: round(v[0] / reps, 4) for k, v in prof.items()}}
+        print(json.dumps({"case": "gemm", "products": out}))
+        return
     if case in ("fom", "fomfull", "pod", "podstream"):
         Nt = 10 if case == "fom" else prob.Nt
         snaps = torch.empty((n_train, Nt, prob.N), dtype=torch.float64, device=dev)
@@ -1124,7 +1161,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=200)
     ap.add_argument("--case", default=None, help="run one profiling workload: fom, fomfull, pod, podstream, solve, spatial, "
-                         "residual, mlp; c3 (the full-size 2-D S6 configuration, streamed by parameter group); "
+                         "residual, mlp, gemm; c3 (the full-size 2-D S6 configuration, streamed by parameter group); "
                          "certificate (Theorem 3's bound with the library's constant)")
     ap.add_argument("--cert-tol", type=float, default=1e-4, help="certificate: power-iteration tolerance")
     ap.add_argument("--cert-iters", type=int, default=300, help="certificate: power-iteration cap")
