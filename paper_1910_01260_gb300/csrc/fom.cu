@@ -351,34 +351,8 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
     for (int k = 0; k < a.Nt; ++k) {
         const double h = a.dt[k];
         const double* uk = a.hist + (size_t)(k % kHist) * vecsz;  // the previous level u^k
-        // ---- Phase X0: initial iterate by extrapolating the last levels in time
-        if (k > 0) {
-            const int o = min(k, kPred);
-            double coef[kPred + 1];  // (-1)^i C(o+1, i+1)
-            {
-                double bin = 1.0;  // C(o+1, i) as i grows
-#pragma unroll
-                for (int i = 0; i <= kPred; ++i) {
-                    bin = bin * (double)(o + 1 - i) / (double)(i + 1);  // C(o+1, i+1)
-                    coef[i] = i <= o ? ((i & 1) ? -bin : bin) : 0.0;
-                }
-            }
-            ROWS_BEGIN
-                double x0[VEC];
-#pragma unroll
-                for (int u = 0; u < VEC; ++u) x0[u] = 0.0;
-#pragma unroll
-                for (int i = 0; i <= kPred; ++i) {
-                    if (i > o) break;
-                    double ui[VEC];
-                    ld_vec<VEC>(a.hist + (size_t)((k - i + kHist * kPred) % kHist) * vecsz + vi, ui);
-#pragma unroll
-                    for (int u = 0; u < VEC; ++u) x0[u] = fma(coef[i], ui[u], x0[u]);
-                }
-                st_vec<VEC>(a.x + vi, x0);
-            ROWS_END
-            if (!grid_sync(a.bar, &s_flag)) return;
-        }
+        // (the initial iterate x0 of this step was formed by the previous
+        // step's phase W from the levels it had just completed)
         // ---- Phase R: b = u^k + h B f^k, r = b - K x0 = b - x0 + h A x0, r^ = r
         {
             double c[NSLOT][VEC];
@@ -649,7 +623,22 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
             }
             __syncthreads();
         }
-        // ---- Phase W: emit snapshot column k, zero solutions, bookkeeping
+        // ---- Phase W: emit snapshot column k, zero solutions, bookkeeping,
+        // and the next step's initial iterate by extrapolating the last
+        // levels in time (a thread's own rows only: the barrier below orders
+        // it before the next step's products)
+        //   x0 = sum_{i=0}^{o} (-1)^i C(o+1, i+1) u^{k+1-i},  o = min(k+1, kPred)
+        const bool extrap = k + 1 < a.Nt;
+        const int o = min(k + 1, kPred);
+        double coef[kPred + 1];  // (-1)^i C(o+1, i+1)
+        {
+            double bin = 1.0;  // C(o+1, i) as i grows
+#pragma unroll
+            for (int i = 0; i <= kPred; ++i) {
+                bin = bin * (double)(o + 1 - i) / (double)(i + 1);  // C(o+1, i+1)
+                coef[i] = i <= o ? ((i & 1) ? -bin : bin) : 0.0;
+            }
+        }
         ROWS_BEGIN
             double xv[VEC];
             ld_vec<VEC>(a.x + vi, xv);
@@ -664,8 +653,23 @@ __global__ void __launch_bounds__(NT, ST_FOM_BLOCKS_PER_SM) fom_march_kernel(Fom
                 }
                 if (p < a.n_mu) __stcs(a.snap + ((int64_t)p * a.Nt + k) * N + row, xv[u]);
             }
-            if (changed) st_vec<VEC>(a.x + vi, xv);
             st_vec<VEC>(a.hist + (size_t)((k + 1) % kHist) * vecsz + vi, xv);
+            if (extrap) {
+                double x0[VEC];
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) x0[u] = fma(coef[0], xv[u], 0.0);
+#pragma unroll
+                for (int i = 1; i <= kPred; ++i) {
+                    if (i > o) break;
+                    double ui[VEC];
+                    ld_vec<VEC>(a.hist + (size_t)((k + 1 - i + kHist * kPred) % kHist) * vecsz + vi, ui);
+#pragma unroll
+                    for (int u = 0; u < VEC; ++u) x0[u] = fma(coef[i], ui[u], x0[u]);
+                }
+                st_vec<VEC>(a.x + vi, x0);
+            } else if (changed) {
+                st_vec<VEC>(a.x + vi, xv);
+            }
         ROWS_END
         if (bid == 0 && threadIdx.x < a.n_mu) {
             const int p = threadIdx.x;
