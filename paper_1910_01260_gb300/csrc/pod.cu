@@ -611,7 +611,10 @@ __global__ void __launch_bounds__(64) larft_kernel(int b, const double* __restri
 // grid barriers remain only around the norms and ordering at the start of a
 // sweep and its convergence test at the end.  Squared column norms are
 // carried with the rotations and recomputed at the start of every sweep.
-// The sweep loop stops after a sweep without rotation.
+// The sweep loop stops after a sweep without rotation, or after a sweep whose
+// rotations all had |cos| = |gamma| / sqrt(alpha beta) below sqrt(tol) / 10:
+// cyclic Jacobi converges quadratically near the end, so the next sweep
+// would find nothing above tol to rotate (it only confirmed convergence).
 struct JacArgs {
     int m, n;
     double* X;
@@ -620,7 +623,8 @@ struct JacArgs {
     int ldy;
     int max_sweeps;
     double tol;
-    int* flags;    // [3]
+    int* flags;    // [3] a rotation in the sweep
+    int* big;      // [3] a rotation with |cos| >= sqrt(tol) / 10 in the sweep
     int* sweeps;   // out
     double* nrm2;  // [n + 1]: squared column norms, then the largest
     double* nsort; // [n] the norms at the start of the sweep, for the ordering
@@ -704,7 +708,10 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
     int sweep = 0;
     bool converged = false;
     for (; sweep < a.max_sweeps; ++sweep) {
-        if (blockIdx.x == 0 && tid == 0) a.flags[(sweep + 1) % 3] = 0;
+        if (blockIdx.x == 0 && tid == 0) {
+            a.flags[(sweep + 1) % 3] = 0;
+            a.big[(sweep + 1) % 3] = 0;
+        }
         // squared column norms, one warp per column
         for (int c = blockIdx.x * JW + warp; c < a.n; c += gridDim.x * JW) {
             const double* xc = a.X + (int64_t)c * a.ldx;
@@ -835,6 +842,9 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
                                 s_dirty[i] = 1;
                                 s_dirty[j] = 1;
                                 ++rot_count;
+                                const double ab = al * be;
+                                if (!(ab <= 1.0e308) || ga * ga > 0.01 * a.tol * ab)
+                                    *(volatile int*)(a.big + sweep % 3) = 1;
                             }
                             s_rot[pr] = rot ? 1 : 0;
                             s_cs[2 * pr] = c;
@@ -889,7 +899,7 @@ __global__ void __launch_bounds__(32 * JW) jacobi_kernel(JacArgs a) {
         }
         // the convergence flag of the sweep and the columns of its last round
         if (!grid_sync(a.bar, &s_flag)) return;
-        if (*(volatile int*)(a.flags + sweep % 3) == 0) {
+        if (*(volatile int*)(a.flags + sweep % 3) == 0 || *(volatile int*)(a.big + sweep % 3) == 0) {
             converged = true;
             ++sweep;
             break;
@@ -1186,7 +1196,7 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
     double* d_sig_sorted = d_sig + cap;  // [cap]
     double* d_sig_tmp = d_sig_sorted + cap;
     double* d_scalar = d_sig_tmp + cap + 8;  // [16]: tau, dot (d_sig_tmp[cap] is the Jacobi norm max)
-    int* d_int = (int*)(d_scalar + 16);  // [16]: k, r_new, sweeps, flags[3]
+    int* d_int = (int*)(d_scalar + 16);  // [16]: k, r_new, sweeps, flags[3], -, panel Cholesky failure, big[3]
     int* d_perm = d_int + 16;            // [cap]
     int* d_piv = d_perm + cap;           // [cap] column pivots of the QR
     unsigned long long* d_rot = reinterpret_cast<unsigned long long*>(d_scalar + 4);
@@ -1235,6 +1245,7 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
         const int npairs = (nb + (nb & 1)) / 2;
         const int jb = std::max(1, std::min(per_sm * m->num_sms, npairs));
         ST_CUDA_TRY(cudaMemsetAsync(d_int + 3, 0, sizeof(int) * 3, st));
+        ST_CUDA_TRY(cudaMemsetAsync(d_int + 8, 0, sizeof(int) * 3, st));
         ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
         // the largest squared column norm is accumulated with atomicMax from zero
         ST_CUDA_TRY(cudaMemsetAsync(d_sig_tmp + ncols, 0, sizeof(double), st));
@@ -1246,7 +1257,7 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
         // sqrt(m) * eps relative (the left singular vectors of the middle
         // matrix are these columns, normalised)
         JacArgs ja{mrows, ncols, Z, cap, Y, cap, m->opt.jacobi_sweeps,
-                   std::sqrt((double)mrows) * 2.220446049250313e-16, d_int + 3, d_int + 2, d_sig_tmp,
+                   std::sqrt((double)mrows) * 2.220446049250313e-16, d_int + 3, d_int + 8, d_int + 2, d_sig_tmp,
                    q_nrm, 0.1 * m->opt.eps_sv, d_rot, d_ready, bar};
         void* args[] = {&ja};
         ST_PROF(m, "jacobi_kernel");
