@@ -58,10 +58,10 @@ ONLINE_REFINE = 2
 # kernels, scaled to a launch by the units it processes (the captures and
 # their commands are summarised under profiles/)
 NCU_DRAM_BYTES = {
-    # profiles/fom_march_kernel_c4_16mu_10steps_subgrids.md: 112.9 MB + 307.5 MB
-    # for 10 steps of the 16-parameter march in 8 sub-grids (reduce-scatter
-    # partials, balanced rows); per step of the march
-    "fom_march_kernel": {"per": "step", "bytes": (112.852224e6 + 307.465728e6) / 10},
+    # profiles/fom_march_kernel_c4_16mu_10steps_subgrids.md: 174.1 MB + 328.4 MB
+    # for 10 steps of the 16-parameter march in 8 sub-grids (the current
+    # kernel); per step of the march
+    "fom_march_kernel": {"per": "step", "bytes": (174.078976e6 + 328.422912e6) / 10},
 }
 # dependence threshold of the incremental SVD, relative to the block's largest
 # column: the value of the paper's first numerical example (Sec. 6); the
