@@ -83,7 +83,7 @@ __global__ void colnorm_max_kernel(int m, int chunks, const double* __restrict__
 struct Gs2Args {
     int64_t N;
     int m;          // columns of E
-    double* E;      // N x m (ld N), overwritten
+    double* E;      // N x m (ld N), scratch: its contents are undefined on return
     double* J;      // N x m (ld N) output directions
     double* P;      // coefficients, column j at P + j * ldp, zeroed by the host
     int ldp;
@@ -92,12 +92,41 @@ struct Gs2Args {
     double* partial;    // [2 x grid x (m + 2)]
     unsigned long long* work;  // accumulated: multiply-adds per row (the flop count is 2 N times it)
     GridBarrier bar;
+    int64_t rs;  // rows per block (the last block may own fewer)
+    int ks;      // directions whose rows of the block are kept in shared memory
 };
 
-// Shared memory of gs2_kernel: the four coefficient vectors.
-inline size_t gs2_smem(int m) { return sizeof(double) * 4 * (size_t)m; }
+// Shared memory of gs2_kernel: the four coefficient vectors, with E_SMEM a
+// ring of three columns of E, then the first ks directions (block rows).
+inline size_t gs2_smem(int m, int64_t rs, bool e_smem, int ks) {
+    return sizeof(double) * (4 * (size_t)m + (e_smem ? 3 * (size_t)rs : 0) + (size_t)ks * (size_t)rs);
+}
 
-__global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Every block owns rows [r0, r0 + R) of E and J.  The block's rows of the
+// three columns in flight (with E_SMEM) and of the first ks directions stay
+// in shared memory; the column after them is fetched by asynchronous copies
+// one column ahead.  Updates are row-local; dot products are a warp per
+// value over the block's rows, then across blocks: a reduction writes
+// per-block partials (slots 0..m-1 dots, m the squared norm, m+1 the cross
+// term) to one of two buffers, alternating, and every block sums all
+// blocks' partials in a fixed order, so a buffer is rewritten only two
+// barriers after it was read.  The norm of column j, its product with
+// column j+1 and the first-pass projections of column j+1 share one
+// reduction (the coefficient on a direction accepted from column j is
+// e_j^T e_{j+1} / ||e_j||): two grid barriers per column.  The work of a
+// column is small, so the code a column runs through is kept small too
+// (loops whose bodies every warp reuses, one body for both passes): its
+// instructions are fetched from the SM's caches, not from L2.
+template <bool E_SMEM>
+__global__ void __launch_bounds__(NT, 1) gs2_kernel(Gs2Args a) {
     extern __shared__ double sm[];
     // pass-1 / pass-2 coefficients of the column being finished (hc, h2c)
     // and of the column being projected (hn, h2n); swapped every column
@@ -105,207 +134,192 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
     double* h2c = sm + a.m;
     double* hn = sm + 2 * (size_t)a.m;
     double* h2n = sm + 3 * (size_t)a.m;
-    __shared__ double s_w1[NWARP], s_w2[NWARP];
+    double* s_e = sm + 4 * (size_t)a.m;                    // [3][rs] with E_SMEM
+    double* s_j = s_e + (E_SMEM ? 3 * (size_t)a.rs : 0);  // [ks][rs]
     __shared__ double s_nu, s_inv, s_cross;
     __shared__ int s_flag;
     const int G = gridDim.x, b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t R = (a.N + G - 1) / G;
-    const int64_t r0 = (int64_t)b * R, r1 = min(a.N, r0 + R);
-    // element i of column j of E, of direction c of J
-    auto e_ld = [&](int j, int64_t i) -> double { return __ldcg(a.E + (int64_t)j * a.N + i); };
-    auto e_st = [&](int j, int64_t i, double v) { __stcg(a.E + (int64_t)j * a.N + i, v); };
-    auto j_ld = [&](int c, int64_t i) -> double { return __ldcg(a.J + (int64_t)c * a.N + i); };
+    const int64_t r0 = (int64_t)b * a.rs;
+    const int R = (int)max((int64_t)0, min(a.N, r0 + a.rs) - r0);
+    const int64_t rs = a.rs;
+    const int ks = a.ks;
+    const int m = a.m;
+    // this block's rows of column c of E and of direction c of J
+    auto e_col = [&](int c) -> double* {
+        if (E_SMEM) return s_e + (size_t)(c % 3) * rs;
+        return a.E + (int64_t)c * a.N + r0;
+    };
+    auto j_col = [&](int c) -> double* {
+        return c < ks ? s_j + (size_t)c * rs : a.J + (int64_t)c * a.N + r0;
+    };
+    // a thread leaves only after its asynchronous copies have landed
+    auto leave = [&]() {
+        if (E_SMEM) cp_async_wait_all();
+    };
+    // this thread's share of column c into its ring slot (one copy group,
+    // committed even when empty so that the group count stays aligned)
+    auto prefetch = [&](int c) {
+        if (!E_SMEM) return;
+        if (c < m) {
+            double* dst = e_col(c);
+            const double* src = a.E + (int64_t)c * a.N + r0;
+#pragma unroll 1
+            for (int r = tid; r < R; r += NT) cp_async8(dst + r, src + r);
+        }
+        cp_async_commit();
+    };
     const double tau = a.tau ? *a.tau : -1.0;
-    // Every block owns rows [r0, r1) of E and J: updates are local and only
-    // dot products cross blocks.  A reduction writes per-block partials
-    // (slots 0..m-1 dots, m the squared norm, m+1 the cross term) to one of
-    // two buffers, alternating, and every block sums all blocks' partials in
-    // a fixed order, so a buffer is rewritten only two barriers after it was
-    // read.  The norm of column j, its product with column j+1 and the
-    // first-pass projections of column j+1 share one reduction (the
-    // coefficient on a direction accepted from column j is e_j^T e_{j+1} /
-    // ||e_j||): two grid barriers per column.  A dependent FP64 add costs tens
-    // of cycles on this GPU, so the sums below are pairwise and the dot
-    // products keep four independent accumulators.
-    const int S = a.m + 2;
+    const int S = m + 2;
     int red = 0;
-    auto part = [&](int slot) { return a.partial + ((size_t)(red & 1) * G + b) * S + slot; };
     auto part_of = [&](int bb, int slot) { return a.partial + ((size_t)(red & 1) * G + bb) * S + slot; };
-    // block sums of two per-thread values, written by thread 0 to slots m, m+1
-    auto write_pair = [&](double v1, double v2) {
-        v1 = warp_sum(v1);
-        v2 = warp_sum(v2);
-        if (lane == 0) {
-            s_w1[warp] = v1;
-            s_w2[warp] = v2;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double t1[NWARP], t2[NWARP];
-#pragma unroll
-            for (int w = 0; w < NWARP; ++w) {
-                t1[w] = s_w1[w];
-                t2[w] = s_w2[w];
-            }
-#pragma unroll
-            for (int h = NWARP / 2; h > 0; h >>= 1)
-#pragma unroll
-                for (int w = 0; w < h; ++w) {
-                    t1[w] += t1[w + h];
-                    t2[w] += t2[w + h];
+    // Block partials of nv values, a warp per value: value q < nj is
+    // J(:, q)^T y, value nj is v^T v and nj+1 is v^T y (v, y columns of E, y
+    // < 0 a zero column); the partial of value q goes to slot q (q < nj) or
+    // m + q - nj.  Lane-strided rows, two accumulators, then the warp.
+    auto block_dots = [&](int nj, int nv, int vc, int yc) {
+        const double* v = e_col(vc);
+        const double* y = yc >= 0 ? e_col(yc) : nullptr;
+#pragma unroll 1
+        for (int q = warp; q < nv; q += NWARP) {
+            const double* x = q < nj ? j_col(q) : v;
+            const double* z = q == nj ? v : y;
+            double s0 = 0.0, s1 = 0.0;
+            if (z) {
+                int r = lane;
+#pragma unroll 1
+                for (; r + 32 < R; r += 64) {
+                    s0 = fma(x[r], z[r], s0);
+                    s1 = fma(x[r + 32], z[r + 32], s1);
                 }
-            __stcg(part(a.m), t1[0]);
-            __stcg(part(a.m + 1), t2[0]);
+                if (r < R) s0 = fma(x[r], z[r], s0);
+            }
+            const double t = warp_sum(s0 + s1);
+            if (lane == 0) __stcg(part_of(b, q < nj ? q : m + (q - nj)), t);
         }
     };
-    // fixed-order sum over the blocks of one partial slot (lane-strided,
-    // pairwise, then across the warp); the loads of eight blocks per lane are
-    // in flight together (one round for up to 256 blocks)
-    auto sum_slot = [&](int slot) -> double {
-        double acc = 0.0;
-        for (int b0 = lane; b0 < G; b0 += 8 * 32) {
-            double v[8];
+    // Fixed-order sums over the blocks of ns slots (slot q for q < nq, m +
+    // q - nq after), a warp per slot, the loads of eight blocks per lane in
+    // flight together: h[q] for q < nq, then ||e||, 1/||e|| and the cross
+    // term.
+    auto sum_slots = [&](int nq, int ns, double* h) {
+#pragma unroll 1
+        for (int q = warp; q < ns; q += NWARP) {
+            const int sl = q < nq ? q : m + (q - nq);
+            double acc = 0.0;
+#pragma unroll 1
+            for (int b0 = lane; b0 < G; b0 += 8 * 32) {
+                double v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int bb = b0 + 32 * i;
-                v[i] = bb < G ? __ldcg(part_of(bb, slot)) : 0.0;
+                for (int i = 0; i < 8; ++i) {
+                    const int bb = b0 + 32 * i;
+                    v[i] = bb < G ? __ldcg(part_of(bb, sl)) : 0.0;
+                }
+                acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
             }
-            acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-        }
-        return warp_sum(acc);
-    };
-    // dot product of this block's rows of direction c and column j (lane-
-    // strided, four independent accumulators, then across the warp)
-    auto block_dot = [&](int c, int j) -> double {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int64_t i0 = r0 + lane; i0 < r1; i0 += 4 * 32) {
-            double xv[4], yv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t i = i0 + 32 * u;
-                xv[u] = i < r1 ? j_ld(c, i) : 0.0;
-                yv[u] = i < r1 ? e_ld(j, i) : 0.0;
+            const double t = warp_sum(acc);
+            if (lane == 0) {
+                if (q < nq) h[q] = t;
+                else if (q == nq) {
+                    // ||e_j|| and its inverse from one reciprocal square root
+                    // (a zero column: both zero; Inf or NaN: a non-finite norm)
+                    const double iv = t > 0.0 ? rsqrt(t) : 0.0;
+                    s_inv = iv;
+                    s_nu = t > 0.0 ? t * iv : (t == 0.0 ? 0.0 : t);
+                } else s_cross = t;
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] = fma(xv[u], yv[u], acc[u]);
         }
-        return warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
     };
     int k = 0;   // directions found so far
     int kc = 0;  // directions the finishing column was projected on
     unsigned long long work = 2;  // multiply-adds per row: ||e_0||^2 and e_0^T e_1
-    {
-        // column 0 has nothing to project: ||e_0||^2 and e_0^T e_1
-        double n2 = 0.0, cr = 0.0;
-        for (int64_t i = r0 + tid; i < r1; i += NT) {
-            const double v = e_ld(0, i);
-            n2 = fma(v, v, n2);
-            if (a.m > 1) cr = fma(v, e_ld(1, i), cr);
-        }
-        write_pair(n2, cr);
-    }
-    for (int j = 0; j < a.m; ++j) {
+    prefetch(0);
+    prefetch(1);
+    prefetch(2);
+    leave();
+    __syncthreads();
+    // column 0 has nothing to project: ||e_0||^2 and e_0^T e_1
+    block_dots(0, 2, 0, m > 1 ? 1 : -1);
+#pragma unroll 1
+    for (int j = 0; j < m; ++j) {
         // reduction A: ||e_j||^2, e_j^T e_{j+1}, J(:, 0:k)^T e_{j+1}
-        if (!grid_sync(a.bar, &s_flag)) return;
-        const int kn = k;
-        // slots 0..kn-1: coefficients; then the squared norm and the cross term
-        for (int c = warp; c < kn + 2; c += NWARP) {
-            const double acc = sum_slot(c < kn ? c : a.m + (c - kn));
-            if (lane == 0) {
-                if (c < kn) hn[c] = acc;
-                else if (c == kn) {
-                    // ||e_j|| and its inverse from one reciprocal square root
-                    const double iv = acc > 0.0 ? rsqrt(acc) : 0.0;
-                    s_inv = iv;
-                    s_nu = acc > 0.0 ? acc * iv : sqrt(acc);
-                } else s_cross = acc;
-            }
+        if (!grid_sync(a.bar, &s_flag)) {
+            leave();
+            return;
         }
+        sum_slots(k, k + 2, hn);
         ++red;
         __syncthreads();
         const double nu = s_nu;
         if (!isfinite(nu)) {
             if (tid == 0) grid_abort(a.bar, ST_ERR_NONFINITE);
+            leave();
             return;
         }
         // finish column j: its coefficients, and a new direction if the
         // remainder is above the threshold
         if (b == 0)
+#pragma unroll 1
             for (int c = tid; c < kc; c += NT) a.P[c + (int64_t)j * a.ldp] = hc[c] + h2c[c];
         if (nu > tau && nu > 0.0) {
             const double inv = s_inv;
-            double* jk = a.J + (int64_t)k * a.N;
-            for (int64_t i = r0 + tid; i < r1; i += NT) __stcg(jk + i, e_ld(j, i) * inv);
+            const double* ej = e_col(j);
+            double* jk = a.J + (int64_t)k * a.N + r0;
+            double* sk = k < ks ? s_j + (size_t)k * rs : jk;
+#pragma unroll 1
+            for (int r = tid; r < R; r += NT) {
+                const double v = ej[r] * inv;
+                sk[r] = v;
+                __stcg(jk + r, v);
+            }
             if (b == 0 && tid == 0) a.P[k + (int64_t)j * a.ldp] = nu;
             if (tid == 0) hn[k] = s_cross * inv;
             ++k;
         }
         __syncthreads();
-        if (j + 1 == a.m) break;
+        if (j + 1 == m) break;
+        // column j's ring slot is free (its last reads precede the barrier)
+        prefetch(j + 3);
         // both passes' updates and dot products, the next column's first-pass
         // dot products, the squared norm and the cross term
-        work += 3 * (unsigned long long)k + (j + 2 < a.m ? k : 0) + 2;
-        // column j+1: first pass e -= J(:, 0:k) hn, second-pass projections
-        if (k > 0) {
-            // two rows per pass of the loop: their chains of k FMAs interleave
-            for (int64_t i = r0 + tid; i < r1; i += 2 * NT) {
-                const int64_t i2 = i + NT;
-                const bool two = i2 < r1;
-                double v = e_ld(j + 1, i), v2 = two ? e_ld(j + 1, i2) : 0.0;
-                for (int c = 0; c < k; ++c) {
-                    const double h = hn[c];
-                    v = fma(-j_ld(c, i), h, v);
-                    if (two) v2 = fma(-j_ld(c, i2), h, v2);
+        work += 3 * (unsigned long long)k + (j + 2 < m ? k : 0) + 2;
+        // pass 0 (with directions): e_{j+1} -= J hn, then J^T e_{j+1}, reduced
+        // into h2n; pass 1: e_{j+1} -= J h2n, then the first-pass products of
+        // e_{j+2}, ||e_{j+1}||^2 and e_{j+1}^T e_{j+2}
+        double* e1 = e_col(j + 1);
+#pragma unroll 1
+        for (int pass = k > 0 ? 0 : 1; pass < 2; ++pass) {
+            const double* h = pass ? h2n : hn;
+            if (k > 0)
+#pragma unroll 1
+                for (int r = tid; r < R; r += NT) {
+                    double v = e1[r], w = 0.0;
+                    int c = 0;
+#pragma unroll 1
+                    for (; c + 1 < k; c += 2) {
+                        v = fma(-j_col(c)[r], h[c], v);
+                        w = fma(-j_col(c + 1)[r], h[c + 1], w);
+                    }
+                    if (c < k) v = fma(-j_col(c)[r], h[c], v);
+                    e1[r] = v + w;
                 }
-                e_st(j + 1, i, v);
-                if (two) e_st(j + 1, i2, v2);
-            }
+            if (E_SMEM && pass == 1) cp_async_wait_all_but_one();  // column j+2 has landed
             __syncthreads();
-            for (int c = warp; c < k; c += NWARP) {
-                const double acc = block_dot(c, j + 1);
-                if (lane == 0) __stcg(part(c), acc);
+            if (pass == 0) {
+                block_dots(k, k, j + 1, j + 1);
+                // reduction B: J(:, 0:k)^T e_{j+1} (second pass)
+                if (!grid_sync(a.bar, &s_flag)) {
+                    leave();
+                    return;
+                }
+                sum_slots(k, k, h2n);
+                ++red;
+                __syncthreads();
+            } else {
+                block_dots(k, k + 2, j + 1, j + 2 < m ? j + 2 : -1);
             }
-            // reduction B: J(:, 0:k)^T e_{j+1} (second pass)
-            if (!grid_sync(a.bar, &s_flag)) return;
-            for (int c = warp; c < k; c += NWARP) {
-                const double acc = sum_slot(c);
-                if (lane == 0) h2n[c] = acc;
-            }
-            ++red;
-            __syncthreads();
         }
         kc = k;
-        // second-pass update of e_{j+1} with its squared norm and its product
-        // with e_{j+2}, and the first-pass projections of e_{j+2}
-        const bool has2 = j + 2 < a.m;
-        double n2 = 0.0, cr = 0.0;
-        for (int64_t i = r0 + tid; i < r1; i += 2 * NT) {
-            const int64_t i2 = i + NT;
-            const bool two = i2 < r1;
-            double v = e_ld(j + 1, i), v2 = two ? e_ld(j + 1, i2) : 0.0;
-            if (k > 0) {
-                for (int c = 0; c < k; ++c) {
-                    const double h = h2n[c];
-                    v = fma(-j_ld(c, i), h, v);
-                    if (two) v2 = fma(-j_ld(c, i2), h, v2);
-                }
-                e_st(j + 1, i, v);
-                if (two) e_st(j + 1, i2, v2);
-            }
-            n2 = fma(v, v, n2);
-            if (has2) cr = fma(v, e_ld(j + 2, i), cr);
-            if (two) {
-                n2 = fma(v2, v2, n2);
-                if (has2) cr = fma(v2, e_ld(j + 2, i2), cr);
-            }
-        }
-        if (has2)
-            for (int c = warp; c < k; c += NWARP) {
-                const double acc = block_dot(c, j + 2);
-                if (lane == 0) __stcg(part(c), acc);
-            }
-        write_pair(n2, cr);
         double* t = hc;
         hc = hn;
         hn = t;
@@ -313,6 +327,7 @@ __global__ void __launch_bounds__(NT, 2) gs2_kernel(Gs2Args a) {
         h2c = h2n;
         h2n = t;
     }
+    leave();
     if (b == 0 && tid == 0) {
         *a.k_out = k;
         if (a.work) atomicAdd(a.work, work);
@@ -1152,16 +1167,39 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
     // buffers
     const size_t szW2 = (size_t)N * cap, szV2 = (size_t)ldv * rcap, szE = (size_t)N * bmax,
                  szL = (size_t)rcap * bmax, szP = (size_t)pdim * pdim, szX = (size_t)cap * cap;
-    int gs_blocks = 0;
+    // Gram-Schmidt kernel: one block per SM, gs_rs rows each
+    const int gs_blocks = (int)std::min<int64_t>(m->num_sms, std::max<int64_t>(1, N / 64));
+    const int64_t gs_rs = (N + gs_blocks - 1) / gs_blocks;
+    int gs_smem_max = 0;
     {
-        int per_sm = 0;
-        size_t smem = gs2_smem(pdim);
-        if (smem > 48 * 1024)
-            ST_CUDA_TRY(cudaFuncSetAttribute(gs2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gs2_kernel, NT, smem));
-        gs_blocks = std::max(1, std::min(per_sm, 1)) * m->num_sms;
-        gs_blocks = (int)std::min<int64_t>(gs_blocks, std::max<int64_t>(1, N / 64));
+        int dev = 0;
+        ST_CUDA_TRY(cudaGetDevice(&dev));
+        ST_CUDA_TRY(cudaDeviceGetAttribute(&gs_smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     }
+    // launch of gs2_kernel on g.m columns: the block's rows of three columns
+    // of E in shared memory when they fit, and as many directions as fit
+    auto launch_gs2 = [&](Gs2Args g) -> st_status {
+        cudaFuncAttributes fa{};
+        ST_CUDA_TRY(cudaFuncGetAttributes(&fa, gs2_kernel<true>));
+        const int64_t budget = (int64_t)gs_smem_max - (int64_t)fa.sharedSizeBytes;
+        const int64_t col = (int64_t)sizeof(double) * gs_rs;
+        const int64_t base = (int64_t)sizeof(double) * 4 * g.m;
+        const bool e_smem = base + 3 * col <= budget;
+        const int64_t room = budget - base - (e_smem ? 3 * col : 0);
+        g.rs = gs_rs;
+        g.ks = (int)std::max<int64_t>(0, std::min<int64_t>(g.m, room / col));
+        const size_t smem = gs2_smem(g.m, gs_rs, e_smem, g.ks);
+        const void* fn = e_smem ? (const void*)gs2_kernel<true> : (const void*)gs2_kernel<false>;
+        ST_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem));
+        if (per_sm < 1) return st_fail(ST_ERR_CUDA, "st_rom_build_basis: Gram-Schmidt kernel does not fit an SM");
+        void* args[] = {&g};
+        ST_PROF(m, "gs2_kernel");
+        ST_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(gs_blocks), dim3(NT), args, smem, st));
+        st_count_launch();
+        return ST_OK;
+    };
     const size_t szPart = std::max((size_t)2 * std::max(gs_blocks, 1) * (pdim + 2), (size_t)64 * bmax);
     const size_t szPan = (size_t)pdim * kGsPanel + 4 * (size_t)kGsPanel * kGsPanel;
     const size_t doubles = szW2 + szV2 + szE + 2 * szL + 3 * szP + 3 * szX + (size_t)cap * rcap * 2 +
@@ -1308,14 +1346,7 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
             }
             ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
             double* Jn = Jout + (size_t)k * N;
-            Gs2Args g{N, pw, Ep, Jn, Pp + k, ldp, d_int, tau, partial, d_gs_work, bar};
-            void* args[] = {&g};
-            {
-                ST_PROF(m, "gs2_kernel");
-                ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT), args,
-                                                        gs2_smem(pw), st));
-                st_count_launch();
-            }
+            ST_TRY(launch_gs2(Gs2Args{N, pw, Ep, Jn, Pp + k, ldp, d_int, tau, partial, d_gs_work, bar, 0, 0}));
             int kp = 0;
             ST_TRY(read_k(&kp));
             if (k > 0 && kp > 0) {
@@ -1501,12 +1532,7 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
                 ++m->pod_reorth;
                 ST_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)r * r, st));
                 ST_CUDA_TRY(cudaMemsetAsync(m->d_bar, 0, sizeof(unsigned int) * 4, st));
-                Gs2Args g{N, r, W, W2, P, r, d_int, nullptr, partial, d_gs_work, bar};
-                void* args[] = {&g};
-                ST_PROF(m, "gs2_kernel");
-                ST_CUDA_TRY(cudaLaunchCooperativeKernel((void*)gs2_kernel, dim3(gs_blocks), dim3(NT),
-                                                        args, gs2_smem(r), st));
-                st_count_launch();
+                ST_TRY(launch_gs2(Gs2Args{N, r, W, W2, P, r, d_int, nullptr, partial, d_gs_work, bar, 0, 0}));
                 ST_CUDA_TRY(cudaMemcpyAsync(W, W2, sizeof(double) * N * r, cudaMemcpyDeviceToDevice, st));
             }
         }
