@@ -172,14 +172,19 @@ def test_pod_column_stream(pod_cols, r_max):
     m.close()
 
 
-def test_reorthogonalisation_of_a_drifted_basis(monkeypatch):
+@pytest.mark.parametrize("name,lead", [("c1", None), ("c4", 10)])
+def test_reorthogonalisation_of_a_drifted_basis(monkeypatch, name, lead):
     """Algorithm 2's orthogonality check and QR re-orthogonalisation, made to
     fire on the GPU: the state of one update with W drifted from orthogonality
     (W0 (I + delta U), U strictly upper triangular) is installed, the next
     block is folded in, and the result is compared with the oracle's update
-    of the same state."""
+    of the same state.  At c4 (N = 49,152) the re-orthogonalised basis has
+    about 100 columns, more directions than the Gram-Schmidt kernel keeps in
+    shared memory for a block's 324 rows, so the later ones are read from
+    global memory; the leading 10 singular vectors there are separated by
+    relative gaps above 1e-5 (the next ones by as little as 1e-12)."""
     torch = __import__("torch")
-    p = problem_for("c1")
+    p = problem_for(name)
     blocks = oracle_fom(p, p.train_mu[:2])
     W0, s0, V0 = pod.incremental_update(None, None, None, blocks[0], 200, 1e-12, 1e-14)
     r = W0.shape[1]
@@ -197,6 +202,8 @@ def test_reorthogonalisation_of_a_drifted_basis(monkeypatch):
     W_o, s_o, V_o = pod.incremental_update(Wd, s0, V0, blocks[1], 200, 1e-12, 1e-14)
     assert fired == [True]
     m = make_model(p, r_max=200)
+    if name == "c4":
+        assert len(s_o) >= 90
     m.st_pod_set_state(r, p.Nt, dev_tensor(Wd.T.copy()), s0, dev_tensor(V0.T.copy()))
     m.st_pod_update(p.Nt, _snap_tensor(blocks[1:2]), p.Nt)
     sweeps, reorth = m.st_pod_get_stats()
@@ -212,9 +219,9 @@ def test_reorthogonalisation_of_a_drifted_basis(monkeypatch):
     k = min(40, r2, len(s_o))
     assert np.abs(sig[:k] - s_o[:k]).max() < 1e-11 * s_o[0]
     assert np.abs(Wg.T @ Wg - np.eye(r2)).max() < 1e-12
-    # the leading ns directions (well separated singular values): equal up to
+    # the leading directions (well separated singular values): equal up to
     # sign, since the QR keeps each column's orientation
-    lead = p.ns
+    lead = p.ns if lead is None else lead
     assert np.abs(pod.canonical_signs(Wg[:, :lead]) - pod.canonical_signs(W_o[:, :lead])).max() < 1e-9
     # the factorisation itself does not depend on signs
     A_g = Wg @ np.diag(sig) @ Vg.T
