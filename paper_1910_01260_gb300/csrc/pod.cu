@@ -1177,11 +1177,19 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
         ST_CUDA_TRY(cudaDeviceGetAttribute(&gs_smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     }
     // launch of gs2_kernel on g.m columns: the block's rows of three columns
-    // of E in shared memory when they fit, and as many directions as fit
-    auto launch_gs2 = [&](Gs2Args g) -> st_status {
+    // of E in shared memory when they fit, and as many directions as fit.
+    // The function attributes are set (and the fit checked) once per shared
+    // memory size: the launches follow host synchronisations, so host calls
+    // here delay the GPU.
+    size_t gs_smem_set[2] = {0, 0};  // dynamic shared memory set for gs2_kernel<false>, <true>
+    int64_t gs_static = 0;
+    {
         cudaFuncAttributes fa{};
         ST_CUDA_TRY(cudaFuncGetAttributes(&fa, gs2_kernel<true>));
-        const int64_t budget = (int64_t)gs_smem_max - (int64_t)fa.sharedSizeBytes;
+        gs_static = (int64_t)fa.sharedSizeBytes;
+    }
+    auto launch_gs2 = [&](Gs2Args g) -> st_status {
+        const int64_t budget = (int64_t)gs_smem_max - gs_static;
         const int64_t col = (int64_t)sizeof(double) * gs_rs;
         const int64_t base = (int64_t)sizeof(double) * 4 * g.m;
         const bool e_smem = base + 3 * col <= budget;
@@ -1190,10 +1198,14 @@ st_status pod_update_impl(st_model* m, int64_t ncols_all, const double* snapshot
         g.ks = (int)std::max<int64_t>(0, std::min<int64_t>(g.m, room / col));
         const size_t smem = gs2_smem(g.m, gs_rs, e_smem, g.ks);
         const void* fn = e_smem ? (const void*)gs2_kernel<true> : (const void*)gs2_kernel<false>;
-        ST_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem));
-        if (per_sm < 1) return st_fail(ST_ERR_CUDA, "st_rom_build_basis: Gram-Schmidt kernel does not fit an SM");
+        if (gs_smem_set[e_smem] < smem) {
+            ST_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int per_sm = 0;
+            ST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem));
+            if (per_sm < 1)
+                return st_fail(ST_ERR_CUDA, "st_rom_build_basis: Gram-Schmidt kernel does not fit an SM");
+            gs_smem_set[e_smem] = smem;
+        }
         void* args[] = {&g};
         ST_PROF(m, "gs2_kernel");
         ST_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(gs_blocks), dim3(NT), args, smem, st));
